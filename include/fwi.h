@@ -1,0 +1,198 @@
+/*
+ * libfwi -- GB300 (sm_103a) checkpointed full-waveform-inversion gradient with
+ * lossy, error-bounded checkpoint compression.
+ *
+ * Method: Kukreja et al., "Lossy Checkpoint Compression in Full Waveform
+ * Inversion".  The library computes, for one shot, the simulated data
+ * d_sim = P_r A(m)^-1 P_s^T q_s (Sec. 2, Eq. (2)), the misfit
+ * Phi = 1/2 ||d_sim - d_obs||^2 (Eq. (3)) and its gradient with respect to
+ * the squared slowness m (Eq. (4)), keeping the forward wavefield as
+ * checkpoints (Sec. 1.2) that are compressed with a fixed-accuracy block codec
+ * (Sec. 1.3, Fig. 1).
+ *
+ * Conventions shared by every call:
+ *   - Fields are FP32, C order [nz][ny][nx] (x fastest), unpadded, on the
+ *     device unless the name starts with h_.
+ *   - Pointers named d_* are caller-owned device memory; h_* are host memory.
+ *     The library allocates device memory only inside fwi_ckpt_store_create
+ *     (the checkpoint arena, freed by fwi_ckpt_store_destroy) and for the
+ *     per-call working set (wavefields, scan scratch), which it takes from the
+ *     device's stream-ordered memory pool and returns before the call ends.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *     their kernels on it; a call that returns a host scalar (h_out_bytes,
+ *     h_misfit, h_out) synchronises that stream before returning.
+ *   - Every call returns FWI_OK (0) or a negative status; nothing aborts or
+ *     throws across this interface.  fwi_status_string names the codes.
+ */
+#ifndef FWI_H
+#define FWI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define FWI_OK 0
+#define FWI_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, ...) */
+#define FWI_ERR_CAPACITY (-2)  /* output or checkpoint arena too small */
+#define FWI_ERR_CORRUPT (-3)   /* malformed compressed stream */
+#define FWI_ERR_NONFINITE (-4) /* NaN or Inf in a field given to the codec */
+#define FWI_ERR_CUDA (-5)      /* a CUDA runtime call failed */
+#define FWI_ERR_TIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define FWI_ERR_NOMEM (-7)     /* device allocation failed */
+
+/* ---- geometry ------------------------------------------------------------- */
+/* Grid, time axis and absorbing layer (Sec. 3, "Reference Problem": grid with
+ * an absorbing layer on every face, fixed step dt, nt steps).  The nbl-cell
+ * layer is part of the nx*ny*nz grid.  Its damping rate at depth d (m) into
+ * the layer is (3 vmax / 2W) ln(1/sponge_R) (d/W)^2, W = nbl*h, summed over
+ * the three axes, and it multiplies the model given to the call. */
+typedef struct {
+  int nx, ny, nz;
+  double h;        /* grid spacing, m */
+  double dt;       /* time step, s */
+  int nt;          /* number of time steps N */
+  int nbl;         /* absorbing-layer width, cells (0 = none) */
+  double sponge_R; /* target reflection coefficient of the layer, (0,1) */
+  double vmax;     /* reference velocity of the damping profile, m/s */
+} fwi_geometry;
+
+/* ---- checkpoint policy and schedule (Sec. 1.2) ---------------------------- */
+#define FWI_CKPT_FULL 1    /* keep every forward state u^1..u^N */
+#define FWI_CKPT_EVERY_K 2 /* keep the pair (u^{c-1}, u^c) at c = 0, K, 2K, ...;
+                              recompute the states in between during the
+                              reverse sweep */
+typedef struct {
+  int mode;       /* FWI_CKPT_* */
+  int k_or_snaps; /* K for FWI_CKPT_EVERY_K, ignored otherwise */
+  double atol;    /* > 0: compress every checkpoint with this absolute error
+                     tolerance (Sec. 1.3); <= 0: raw FP32 copies */
+} fwi_ckpt_policy;
+
+/* Actions of a schedule: the "forward, store, backward, load and recompute
+ * events" of Sec. 1.2. */
+#define FWI_ACT_ADVANCE 1   /* forward step: u^step -> u^{step+1}, record data d^step */
+#define FWI_ACT_STORE 2     /* store the state at `step` (arg = 1: u^step; 2: u^{step-1}, u^step) */
+#define FWI_ACT_RESTORE 3   /* make the stored state at `step` current (arg as for STORE) */
+#define FWI_ACT_RECOMPUTE 4 /* forward step without recording: u^step -> u^{step+1} */
+#define FWI_ACT_ADJOINT 5   /* adjoint step k = step (lambda_{k-1}) and imaging with u^k */
+typedef struct {
+  int kind;
+  int step;
+  int arg;
+} fwi_action;
+
+/* Fill out[0..cap) with the schedule fwi_gradient executes for nt steps under
+ * pol; *n_out = total number of actions.  Returns FWI_ERR_CAPACITY (with
+ * *n_out set) when cap is smaller; out may be NULL with cap = 0 to query. */
+int fwi_ckpt_schedule(int nt, const fwi_ckpt_policy* pol, fwi_action* out, size_t cap,
+                      size_t* n_out);
+
+/* ---- compressed checkpoint store (Fig. 1: the compressed states handed from
+ * the forward to the reverse sweep) -------------------------------------- */
+typedef struct fwi_ckpt_store fwi_ckpt_store;
+
+/* One device arena of capacity_bytes (cudaMalloc).  Checkpoints are appended
+ * by a device-side cursor, so no host synchronisation happens per checkpoint.
+ * FWI_ERR_NOMEM if the arena cannot be allocated. */
+int fwi_ckpt_store_create(size_t capacity_bytes, fwi_ckpt_store** out);
+int fwi_ckpt_store_destroy(fwi_ckpt_store* st);
+
+typedef struct {
+  size_t capacity_bytes;
+  size_t used_bytes;     /* bytes the last gradient stored (or needed, if it overflowed) */
+  size_t raw_bytes;      /* FP32 bytes of the same checkpoints uncompressed */
+  int n_checkpoints;     /* fields stored by the last gradient */
+  int overflowed;        /* 1 if the last gradient ran out of arena */
+} fwi_store_stats;
+int fwi_ckpt_store_stats(const fwi_ckpt_store* st, fwi_store_stats* out);
+
+/* ---- forward modelling (Sec. 2, Eq. (1)-(2)) ------------------------------ */
+/* Runs u^{n+1} for n = 0..nt-1 from the zero state (or from the given pair
+ * d_u_prev_init = u^{-1}, d_u_cur_init = u^0) and records
+ * d_rec_out[n*nrec + r] = u^{n+1} at receiver r.
+ *   d_m        squared slowness 1/c^2 (s^2/m^2), nx*ny*nz
+ *   h_wavelet  source samples q^0..q^{nt-1} (host), added at (src_i, src_j, src_k)
+ *   d_rec_ijk  nrec (i,j,k) int triples (device), grid nodes
+ *   d_u_prev_out / d_u_last_out   optional: u^{nt-1} and u^{nt}
+ * Scheme: 8th-order Laplacian, 2nd-order leapfrog in time, absorbing layer
+ * (see fwi_geometry). */
+int fwi_forward(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
+                int src_j, int src_k, const int* d_rec_ijk, int nrec, float* d_rec_out,
+                const float* d_u_prev_init, const float* d_u_cur_init, float* d_u_prev_out,
+                float* d_u_last_out, void* stream);
+
+/* ---- gradient (Sec. 2, Eq. (3)-(4); Sec. 1.2-1.3, Fig. 1) ---------------- */
+/* Forward sweep storing checkpoints into st per pol, misfit, adjoint sweep
+ * decompressing them, imaging condition accumulated as
+ *   d_grad += dPhi/dm = -sum_{k=1}^{N} u^k (l_{k-1} - 2 l_k + l_{k+1}) / dt^2
+ * (the damping is held fixed).  *h_misfit = Phi (FP64).  Synchronises.
+ * FWI_ERR_CAPACITY if the arena is too small for the policy (the store's
+ * stats then give the bytes needed); d_grad is left unchanged in that case.
+ * d_obs is nt*nrec, time-major. */
+int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
+                 int src_j, int src_k, const int* d_rec_ijk, int nrec, const float* d_obs,
+                 float* d_grad, double* h_misfit, fwi_ckpt_store* st,
+                 const fwi_ckpt_policy* pol, void* stream);
+
+/* The same gradient with every array in host memory (h_m, h_rec_ijk, h_obs,
+ * h_grad: same layouts as above; pinned memory gives the fastest copies).
+ * Copies inputs to the device, runs fwi_gradient, copies h_grad back
+ * (h_grad += ...).  Synchronises. */
+int fwi_gradient_host(const fwi_geometry* g, const float* h_m, const float* h_wavelet,
+                      int src_i, int src_j, int src_k, const int* h_rec_ijk, int nrec,
+                      const float* h_obs, float* h_grad, double* h_misfit, fwi_ckpt_store* st,
+                      const fwi_ckpt_policy* pol, void* stream);
+
+/* ---- fixed-accuracy codec (Sec. 1.3) -------------------------------------- */
+/* Stream format (shared bit-for-bit with the CPU oracle):
+ *   64-byte header (magic "FCZ1", version, nx, ny, nz, minexp, nblocks,
+ *   chunk size 128, nchunks, payload words, total bytes, format params),
+ *   nchunks u64 chunk word offsets, nblocks u16 block bit lengths (padded to
+ *   8 bytes), then the payload of u64 words.  Each 4x4x4 block (x fastest,
+ *   blocks ordered x, y, z; edge blocks replicate the last plane) carries:
+ *   1 flag bit, 8 bits of block exponent, then embedded bit planes of its 64
+ *   negabinary transform coefficients.  With minexp = floor(log2 atol), every
+ *   decoded value satisfies |x - x'| <= 2^minexp <= atol whenever the block's
+ *   largest exponent is within 24 of minexp (tolerances coarser than FP32's
+ *   own resolution of the block); otherwise |x - x'| < 2^(emax-24). */
+
+/* Worst-case stream size (bytes) for an nx*ny*nz field; 0 on bad sizes. */
+size_t zfp_max_compressed_bytes(int nx, int ny, int nz);
+
+/* Compress d_in with tolerance atol > 0 into d_out (device, out_capacity
+ * bytes).  *h_out_bytes = stream size.  FWI_ERR_CAPACITY (with *h_out_bytes =
+ * the size needed) if out_capacity is too small; FWI_ERR_NONFINITE if d_in
+ * holds NaN or Inf.  Synchronises. */
+int zfp_compress_fixed_accuracy(const float* d_in, int nx, int ny, int nz, double atol,
+                                void* d_out, size_t out_capacity, size_t* h_out_bytes,
+                                void* stream);
+
+/* Decompress a stream of in_bytes bytes into d_out.  FWI_ERR_CORRUPT for a
+ * malformed stream (reads stay inside [d_in, d_in + in_bytes)), FWI_ERR_ARG
+ * if its dimensions differ from nx, ny, nz.  Synchronises. */
+int zfp_decompress(const void* d_in, size_t in_bytes, float* d_out, int nx, int ny, int nz,
+                   void* stream);
+
+/* ---- FP64 reductions ------------------------------------------------------ */
+/* d_resid = d_sim - d_obs (may alias d_sim); *h_misfit = 1/2 sum resid^2 in
+ * FP64 (Eq. (3)).  Synchronises. */
+int fwi_misfit(const float* d_sim, const float* d_obs, size_t n, float* d_resid,
+               double* h_misfit, void* stream);
+
+/* *h_out = sum_i a_i b_i accumulated in FP64 (inner products of the adjoint
+ * and Taylor tests and of the angle metric, Sec. 3.1).  Synchronises. */
+int fwi_dot_f64(const float* d_a, const float* d_b, size_t n, double* h_out, void* stream);
+
+/* ---- misc ----------------------------------------------------------------- */
+const char* fwi_status_string(int status);
+/* Number of kernels this library has launched since load (for accounting). */
+uint64_t fwi_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

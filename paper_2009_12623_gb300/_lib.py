@@ -1,0 +1,99 @@
+"""ctypes binding of libfwi.so (include/fwi.h).  Argument marshalling only.
+
+The library is loaded from this package directory.  There is no fallback: if
+``libfwi.so`` is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfwi.so")
+
+FWI_OK, FWI_ERR_ARG, FWI_ERR_CAPACITY, FWI_ERR_CORRUPT = 0, -1, -2, -3
+FWI_ERR_NONFINITE, FWI_ERR_CUDA, FWI_ERR_TIMEOUT, FWI_ERR_NOMEM = -4, -5, -6, -7
+FWI_CKPT_FULL, FWI_CKPT_EVERY_K = 1, 2
+FWI_ACT_ADVANCE, FWI_ACT_STORE, FWI_ACT_RESTORE, FWI_ACT_RECOMPUTE, FWI_ACT_ADJOINT = 1, 2, 3, 4, 5
+
+#: every symbol include/fwi.h declares
+EXPORTS = [
+    "fwi_ckpt_schedule", "fwi_ckpt_store_create", "fwi_ckpt_store_destroy", "fwi_ckpt_store_stats",
+    "fwi_forward", "fwi_gradient", "fwi_gradient_host", "zfp_max_compressed_bytes",
+    "zfp_compress_fixed_accuracy", "zfp_decompress", "fwi_misfit", "fwi_dot_f64",
+    "fwi_status_string", "fwi_kernel_launch_count",
+]
+
+
+class FwiError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn} failed: {status} ({status_string(status)})")
+
+
+class Geometry(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
+                ("dt", C.c_double), ("nt", C.c_int), ("nbl", C.c_int),
+                ("sponge_R", C.c_double), ("vmax", C.c_double)]
+
+
+class Policy(C.Structure):
+    _fields_ = [("mode", C.c_int), ("k_or_snaps", C.c_int), ("atol", C.c_double)]
+
+
+class Action(C.Structure):
+    _fields_ = [("kind", C.c_int), ("step", C.c_int), ("arg", C.c_int)]
+
+
+class StoreStats(C.Structure):
+    _fields_ = [("capacity_bytes", C.c_size_t), ("used_bytes", C.c_size_t),
+                ("raw_bytes", C.c_size_t), ("n_checkpoints", C.c_int), ("overflowed", C.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libfwi.so (raises if it is absent: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfwi.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, fp, ip, dp = C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)
+        gp, pp = C.POINTER(Geometry), C.POINTER(Policy)
+        L.fwi_ckpt_schedule.argtypes = [C.c_int, pp, C.POINTER(Action), C.c_size_t, C.POINTER(C.c_size_t)]
+        L.fwi_ckpt_store_create.argtypes = [C.c_size_t, C.POINTER(C.c_void_p)]
+        L.fwi_ckpt_store_destroy.argtypes = [vp]
+        L.fwi_ckpt_store_stats.argtypes = [vp, C.POINTER(StoreStats)]
+        L.fwi_forward.argtypes = [gp, fp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, fp,
+                                  fp, fp, fp, fp, vp]
+        L.fwi_gradient.argtypes = [gp, fp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, fp, fp, dp,
+                                   vp, pp, vp]
+        L.fwi_gradient_host.argtypes = L.fwi_gradient.argtypes
+        L.zfp_max_compressed_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
+        L.zfp_max_compressed_bytes.restype = C.c_size_t
+        L.zfp_compress_fixed_accuracy.argtypes = [fp, C.c_int, C.c_int, C.c_int, C.c_double, vp,
+                                                  C.c_size_t, C.POINTER(C.c_size_t), vp]
+        L.zfp_decompress.argtypes = [vp, C.c_size_t, fp, C.c_int, C.c_int, C.c_int, vp]
+        L.fwi_misfit.argtypes = [fp, fp, C.c_size_t, fp, dp, vp]
+        L.fwi_dot_f64.argtypes = [fp, fp, C.c_size_t, dp, vp]
+        L.fwi_status_string.argtypes = [C.c_int]
+        L.fwi_status_string.restype = C.c_char_p
+        L.fwi_kernel_launch_count.argtypes = []
+        L.fwi_kernel_launch_count.restype = C.c_uint64
+        _lib = L
+        return L
+
+
+def status_string(status: int) -> str:
+    return load().fwi_status_string(status).decode()
+
+
+def check(fn: str, status: int) -> None:
+    if status != FWI_OK:
+        raise FwiError(fn, status)

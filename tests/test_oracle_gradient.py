@@ -1,0 +1,148 @@
+"""Pins of the oracle's adjoint sweep, gradient and checkpoint schedules
+(Sec. 2 Eq. (2)-(4); Sec. 1.2 -- checkpointing alone is bitwise exact)."""
+import numpy as np
+import pytest
+
+N = 22
+NT = 70
+H = 10.0
+DT = 1e-3
+
+
+def _case(oracle, nbl=5, nt=NT, seed=0):
+    from paper_2009_12623_gb300 import synth
+    rng = np.random.default_rng(seed)
+    g = oracle.geometry(N, N - 2, N + 1, H, DT, nt, nbl, 1e-3, 3000.0)
+    z = np.arange(N + 1)[:, None, None]
+    v = np.where(z < 10, 1500.0, 2400.0) * np.ones((N + 1, N - 2, N))
+    v *= 1.0 + 0.05 * rng.uniform(-1, 1, size=v.shape)
+    m = 1.0 / v ** 2
+    q = synth.wavelet(nt, DT, 25.0).astype(np.float64)
+    src = (11, 9, 6)
+    rec = np.array([(i, 10, 4) for i in range(3, 19, 2)] + [(7, 4, 15)], dtype=np.int32)
+    return g, m, q, src, rec
+
+
+def test_dot_product_adjoint(oracle):
+    """<F q, d> = <q, F^T d> with F: q -> P_r A^-1 P_s^T q (random q, d)."""
+    rng = np.random.default_rng(1)
+    g, m, _, src, rec = _case(oracle)
+    q = rng.normal(size=NT)
+    d = rng.normal(size=(NT, len(rec)))
+    Fq = oracle.forward(g, m, q, src, rec)
+    Ftd = oracle.adjoint_trace(g, m, d, rec, src)
+    lhs, rhs = np.vdot(Fq, d), np.vdot(q, Ftd)
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
+def test_dot_product_adjoint_no_sponge(oracle):
+    rng = np.random.default_rng(2)
+    g, m, _, src, rec = _case(oracle, nbl=0)
+    q = rng.normal(size=NT)
+    d = rng.normal(size=(NT, len(rec)))
+    lhs = np.vdot(oracle.forward(g, m, q, src, rec), d)
+    rhs = np.vdot(q, oracle.adjoint_trace(g, m, d, rec, src))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def _phi(oracle, g, m, m0, q, src, rec, dobs):
+    d = oracle.forward(g, m, q, src, rec, m0=m0)
+    return 0.5 * np.sum((d - dobs) ** 2)
+
+
+def _obs(oracle, g, m, q, src, rec):
+    m_true = m * (1 + 0.08 * np.exp(-((np.indices(m.shape) - np.array(m.shape)[:, None, None, None] / 2) ** 2).sum(0) / 8.0))
+    return oracle.forward(g, m_true, q, src, rec)
+
+
+def test_gradient_matches_central_differences(oracle):
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    grad, phi, _, _ = oracle.gradient(g, m, q, src, rec, dobs)
+    assert phi == pytest.approx(_phi(oracle, g, m, m, q, src, rec, dobs), rel=1e-13)
+    rng = np.random.default_rng(5)
+    dm = rng.normal(size=m.shape) * m.mean()
+    an = np.vdot(grad, dm)
+    rel = []
+    for eps in (1e-4, 1e-5):
+        fd = (_phi(oracle, g, m + eps * dm, m, q, src, rec, dobs)
+              - _phi(oracle, g, m - eps * dm, m, q, src, rec, dobs)) / (2 * eps)
+        rel.append(abs(fd - an) / abs(an))
+    # the central difference converges to <g, dm> at second order in eps
+    assert rel[1] <= 1e-6, rel
+    assert 50 < rel[0] / rel[1] < 200, rel
+
+
+def test_taylor_second_order(oracle):
+    """|Phi(m + h dm) - Phi(m) - h <g, dm>| = O(h^2) (the linearisation test of
+    Sec. 4.4, whose remainder roughly quadruples per doubling of h)."""
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    grad, phi, _, _ = oracle.gradient(g, m, q, src, rec, dobs)
+    rng = np.random.default_rng(7)
+    dm = rng.normal(size=m.shape) * m.mean() * 0.02
+    hs = [1.0, 0.5, 0.25, 0.125]
+    rem = [abs(_phi(oracle, g, m + h * dm, m, q, src, rec, dobs) - phi - h * np.vdot(grad, dm)) for h in hs]
+    slopes = np.diff(np.log(rem)) / np.diff(np.log(hs))
+    assert np.all(np.abs(slopes - 2.0) < 0.15), slopes
+
+
+def test_gradient_zero_at_true_model(oracle):
+    g, m, q, src, rec = _case(oracle)
+    dobs = oracle.forward(g, m, q, src, rec)
+    grad, phi, _, _ = oracle.gradient(g, m, q, src, rec, dobs)
+    assert phi == 0.0 and np.all(grad == 0.0)
+
+
+@pytest.mark.parametrize("k", [1, 3, 7, 10, NT, NT + 5])
+def test_every_k_raw_bitwise_equals_full_history(oracle, k):
+    """Checkpointing alone keeps the result bitwise identical (Sec. 1.2)."""
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    g_full, phi_full, d_full, _ = oracle.gradient(g, m, q, src, rec, dobs, mode=oracle.CKPT_FULL)
+    g_k, phi_k, d_k, _ = oracle.gradient(g, m, q, src, rec, dobs, mode=oracle.CKPT_EVERY_K, k=k)
+    assert np.array_equal(g_full, g_k) and phi_full == phi_k and np.array_equal(d_full, d_k)
+
+
+def test_compressed_gradient_converges_as_atol_shrinks(oracle):
+    """Lossy checkpoints: the gradient error falls as atol falls and tends to
+    the uncompressed gradient (Sec. 4.4, the PSNR plateau)."""
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    g_ref, *_ = oracle.gradient(g, m, q, src, rec, dobs)
+    errs, cfs = [], []
+    for atol in (1e-1, 1e-3, 1e-5, 1e-7):
+        gz, _, _, nbytes = oracle.gradient(g, m, q, src, rec, dobs, atol=atol)
+        errs.append(np.linalg.norm(gz - g_ref) / np.linalg.norm(g_ref))
+        cfs.append(NT * m.size * 4 / nbytes)
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-4, errs
+    assert all(a >= b for a, b in zip(cfs, cfs[1:])), cfs
+
+
+def test_every_k_compressed_close_to_full(oracle):
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    g_ref, *_ = oracle.gradient(g, m, q, src, rec, dobs)
+    gz, *_ = oracle.gradient(g, m, q, src, rec, dobs, mode=oracle.CKPT_EVERY_K, k=10, atol=1e-6)
+    assert np.linalg.norm(gz - g_ref) / np.linalg.norm(g_ref) < 1e-3
+
+
+@pytest.mark.parametrize("nt,k", [(0, 1), (1, 1), (10, 3), (9, 3), (20, 20), (5, 8)])
+def test_schedule_every_k_structure(oracle, nt, k):
+    acts = oracle.ckpt_schedule(nt, oracle.CKPT_EVERY_K, k)
+    adj = [s for kind, s, _ in acts if kind == oracle.ACT_ADJOINT]
+    assert adj == sorted(set(adj), reverse=True) and adj == list(range(nt, 0, -1))
+    stores = [s for kind, s, _ in acts if kind == oracle.ACT_STORE]
+    assert stores == [0] + [c for c in range(k, nt + 1, k)]
+    adv = [s for kind, s, _ in acts if kind == oracle.ACT_ADVANCE]
+    assert adv == list(range(nt))
+    # recomputation = forward steps not kept: N - (number of stored states) at most
+    rec = sum(1 for kind, *_ in acts if kind == oracle.ACT_RECOMPUTE)
+    assert rec <= nt
+
+
+def test_schedule_full_structure(oracle):
+    acts = oracle.ckpt_schedule(5, oracle.CKPT_FULL)
+    kinds = [a[0] for a in acts]
+    assert kinds == [1, 2] * 5 + [3, 5] * 5
