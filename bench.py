@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Throughput of the checkpointed FWI gradient with lossy checkpoint
+compression (Kukreja et al.) on GB300.
+
+One step = one shot gradient on the Overthrust-shaped workload: 881 x 881 x 287
+grid at 25 m, 40-cell absorbing layer, 2286 steps of 1.75 ms (4000 ms), 8 Hz
+Ricker source near the surface centre, 441 x 441 receivers, full-history
+checkpoints compressed at atol = 1e-4 and held in HBM.  Forward sweep with
+compression of every state, misfit, adjoint sweep with decompression and
+imaging -- the whole hot path.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  The default run finishes in a few minutes.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shot-gradients/s at fixed gradient error"
+UNIT = "shot-gradients/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="fwi", choices=["fwi", "reference"])
+    p.add_argument("--atol", type=float, default=1e-4)
+    p.add_argument("--nt", type=int, default=2286, help="time steps (2286 = 4000 ms)")
+    p.add_argument("--grid", default="881,881,287")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-verify", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- workload
+def workload(args, rank):
+    import numpy as np
+    from paper_2009_12623_gb300 import synth
+    nx, ny, nz = (int(v) for v in args.grid.split(","))
+    # one shot per rank: sources spread along x just under the water surface
+    sx = nx // 2 + (rank * 40) % max(1, nx // 2 - 40)
+    shot = synth.overthrust_like_shot(nx=nx, ny=ny, nz=nz, nt=args.nt, src_xy=(sx, ny // 2))
+    return shot, np.float32
+
+
+def config_dict(args, shot, policy):
+    g = shot.geom
+    return {"workload": f"overthrust-like single-shot gradient {g.nx}x{g.ny}x{g.nz} at {g.h:.0f} m, "
+                        f"nt={g.nt} (dt={g.dt * 1e3:.2f} ms), 8 Hz Ricker, {len(shot.rec)} receivers, "
+                        f"{policy}",
+            "grid": [g.nx, g.ny, g.nz], "nt": g.nt, "atol": args.atol, "checkpoints": policy,
+            "l2_flush": "inputs larger than L2 (0.9 GB fields)", "parallelism": "shot per GPU"}
+
+
+def kernel_bytes(cells, enc_bytes_per_launch):
+    """Algorithmic bytes per launch (halos and scratch excluded)."""
+    return {
+        "stencil_forward": 16.0 * cells,                 # read u^n, u^{n-1}, m; write u^{n+1}
+        "stencil_adjoint_imaging": 28.0 * cells,         # + read u^k, read/write g
+        "zfp_encode": 4.0 * cells + enc_bytes_per_launch,
+        "zfp_decode": 4.0 * cells + enc_bytes_per_launch,
+    }
+
+
+def source_hash(kernel: str) -> str:
+    files = {"stencil_forward": "stencil.cu", "stencil_adjoint_imaging": "stencil.cu",
+             "zfp_encode": "codec.cu", "zfp_decode": "codec.cu"}
+    csrc = os.path.join(ROOT, "paper_2009_12623_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted({files[kernel], "codec_block.cuh", "common.cuh"}):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, launch_scale: float):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != source_hash(kernel):
+        return None
+    return e["dram_bytes_per_launch"] * launch_scale / e.get("cells", 1) if "cells" in e else None
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(shot, u_field=None, threads_note=True):
+    """Time the oracle (as it stands) on a bounded sample of the workload and
+    extrapolate to one shot gradient: forward and adjoint steps on the full
+    grid (per-step cost from nt=1 vs nt=2 runs), codec on a 16-plane slab of
+    a propagated wavefield scaled to the full grid."""
+    import numpy as np
+    import oracle
+    from paper_2009_12623_gb300 import synth
+    g = shot.geom
+    og = oracle.geometry(g.nx, g.ny, g.nz, g.h, g.dt, 1, g.nbl, g.sponge_R, g.vmax)
+    m = synth.slowness2(shot.v0).astype(np.float64)
+    w = shot.wavelet.astype(np.float64)
+    rec = shot.rec[:64]
+
+    def fwd(nt):
+        og.nt = nt
+        t = time.perf_counter()
+        oracle.forward(og, m, w[:nt], shot.src, rec)
+        return time.perf_counter() - t
+
+    def adj(nt):
+        og.nt = nt
+        r = np.ones((nt, len(rec)))
+        t = time.perf_counter()
+        oracle.adjoint_trace(og, m, r, rec, shot.src)
+        return time.perf_counter() - t
+
+    t_fwd = max(1e-9, fwd(2) - fwd(1))
+    t_adj = max(1e-9, adj(2) - adj(1))
+    slab = 16
+    if u_field is None:
+        rng = np.random.default_rng(0)
+        u_field = rng.normal(size=(slab, g.ny, g.nx)).astype(np.float32) * 0.1
+    sl = np.ascontiguousarray(u_field[:slab], dtype=np.float32)
+    t = time.perf_counter()
+    s = oracle.zfp_compress(sl, 1e-4)
+    t_enc = time.perf_counter() - t
+    t = time.perf_counter()
+    oracle.zfp_decompress(s, sl.shape)
+    t_dec = time.perf_counter() - t
+    scale = g.nz / slab
+    per_step = t_fwd + t_adj + (t_enc + t_dec) * scale
+    sec_per_gradient = per_step * g.nt
+    sample = (f"oracle forward+adjoint step on the full {g.nx}x{g.ny}x{g.nz} grid (per-step time from "
+              f"nt=2 minus nt=1 runs: {t_fwd:.2f} s + {t_adj:.2f} s) and codec encode+decode of a "
+              f"{slab}-plane slab of a propagated wavefield at atol=1e-4 ({t_enc + t_dec:.2f} s, "
+              f"x{scale:.1f} to the full grid), extrapolated to {g.nt} steps")
+    return 1.0 / sec_per_gradient, oracle.num_threads(), sample, per_step
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    shot, _ = workload(args, 0)
+    for _ in range(args.warmup):
+        oracle_sample(shot)
+    vals = []
+    t0 = time.perf_counter()
+    cores = None
+    sample = None
+    for _ in range(args.steps):
+        v, cores, sample, _ = oracle_sample(shot)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    policy = f"full-history compressed checkpoints (atol={args.atol:g})"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, shot, policy),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_fwi(args):
+    import numpy as np
+    import torch
+    ws, rank, local, pg = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_12623_gb300 import api, synth
+
+    shot, _ = workload(args, rank)
+    g = shot.geom
+    m0 = torch.from_numpy(synth.slowness2(shot.v0)).to(dev)
+    mt = torch.from_numpy(synth.slowness2(shot.v_true)).to(dev)
+    rec = torch.from_numpy(shot.rec).to(dev)
+    w = shot.wavelet
+    d_obs = api.forward(g, mt, w, shot.src, rec)
+    del mt
+    torch.cuda.synchronize()
+    cells = g.nx * g.ny * g.nz
+
+    free, total = torch.cuda.mem_get_info()
+    reserve = 26 * (1 << 30) + 6 * cells * 4
+    cap = max(1 << 30, free - reserve)
+    store = api.CheckpointStore(cap)
+    policy_mode, policy_k = api.FWI_CKPT_FULL, 1
+    policy = f"full-history compressed checkpoints (atol={args.atol:g})"
+    grad = torch.zeros(g.shape, dtype=torch.float32, device=dev)
+
+    def step():
+        grad.zero_()
+        return api.gradient(g, m0, w, shot.src, rec, d_obs, store, mode=policy_mode, k=policy_k,
+                            atol=args.atol, grad=grad)
+
+    try:
+        step()
+    except api.FwiError as e:
+        if e.status != -2:
+            raise
+        # the arena cannot hold every compressed state: keep pairs every K steps
+        need = store.stats()["used_bytes"]
+        policy_mode, policy_k = api.FWI_CKPT_EVERY_K, max(2, int(np.ceil(2 * need / cap)) + 1)
+        policy = (f"every-{policy_k} compressed checkpoint pairs (atol={args.atol:g}; full history "
+                  f"needs {need / 2**30:.0f} GiB > arena {cap / 2**30:.0f} GiB)")
+        step()
+    torch.cuda.synchronize()
+    stats = store.stats()
+
+    for _ in range(max(0, args.warmup - 1)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region --------------------------------------------------------
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    api.profile_reset()
+    api.profile_enable(True)
+    launches0 = api.kernel_launch_count()
+    barrier(pg)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    phi = None
+    for _ in range(args.steps):
+        _, phi = step()
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(pg)
+    ms = ev0.elapsed_time(ev1)
+    launches = api.kernel_launch_count() - launches0
+    api.profile_enable(False)
+    prof = api.profile_read()
+    clk = clocks.stop()
+    ms_max = max_over_ranks(pg, ms)
+    value = ws * args.steps / (ms_max / 1e3)
+
+    # ---- roofline of the dominant kernel ---------------------------------------
+    pk, peak_kind = peaks()
+    enc_bytes = stats["used_bytes"] / max(1, stats["n_checkpoints"])
+    kb = kernel_bytes(cells, enc_bytes)
+    timed = {k: v for k, v in prof.items() if k in kb and v[1] > 0}
+    dom = max(timed, key=lambda k: timed[k][0])
+    dom_ms, dom_n = timed[dom]
+    achieved = kb[dom] / (dom_ms / dom_n / 1e3) / 1e9
+    kernels = {k: {"launches": n, "total_ms": round(t, 3), "avg_us": round(1e3 * t / n, 2),
+                   "GB/s": round(kb[k] / (t / n / 1e3) / 1e9, 1),
+                   "frac_of_hbm": round(kb[k] / (t / n / 1e3) / 1e9 / pk["hbm_gbs"], 3),
+                   "share_of_step": round(t / ms, 3)}
+               for k, (t, n) in timed.items()}
+    traffic = measured_traffic(dom, cells)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)",
+            "algorithmic_bytes_per_launch": kb[dom]}
+
+    # ---- gradient error at this tolerance vs raw (uncompressed) checkpoints ----
+    verify = None
+    if not args.no_verify:
+        g_lossy = grad.clone()
+        K = 48
+        grad.zero_()
+        try:
+            api.gradient(g, m0, w, shot.src, rec, d_obs, store, mode=api.FWI_CKPT_EVERY_K, k=K,
+                         atol=0.0, grad=grad)
+            num = api.dot_f64(g_lossy - grad, g_lossy - grad)
+            den = api.dot_f64(grad, grad)
+            cos = api.dot_f64(g_lossy, grad) / np.sqrt(api.dot_f64(g_lossy, g_lossy) * den)
+            verify = {"rel_l2_vs_raw_checkpoints": float(np.sqrt(num / den)),
+                      "angle_rad": float(np.arccos(min(1.0, cos))),
+                      "reference": f"same sweeps with raw FP32 checkpoint pairs every {K} steps"}
+        except api.FwiError as e:
+            verify = {"error": str(e)}
+
+    # ---- end to end through the host-memory entry point --------------------------
+    e2e = None
+    if not args.no_e2e:
+        h_m = torch.from_numpy(synth.slowness2(shot.v0)).pin_memory()
+        h_obs = d_obs.cpu().pin_memory()
+        h_rec = torch.from_numpy(shot.rec).pin_memory()
+        h_grad = torch.zeros(g.shape, dtype=torch.float32).pin_memory()
+        del d_obs
+        torch.cuda.empty_cache()
+
+        def hstep():
+            h_grad.zero_()
+            return api.gradient_host(g, h_m, w, shot.src, h_rec, h_obs, store, mode=policy_mode,
+                                     k=policy_k, atol=args.atol, grad=h_grad)
+        hstep()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        torch.cuda.synchronize()
+        barrier(pg)
+        t_e2e = max_over_ranks(pg, time.perf_counter() - t0)
+        e2e = {"value": ws * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_m.numel() * 4 + h_obs.numel() * 4 + h_rec.numel() * 4 +
+                                         h_grad.numel() * 4 + g.nt * 4),
+               "d2h_bytes_per_step": int(h_grad.numel() * 4 + 8),
+               "entry_point": "fwi_gradient_host (pinned host buffers)"}
+
+    # ---- CPU oracle baseline (rank 0, N=1) ------------------------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        slab = None
+        try:
+            gg = api.Geometry(**{**g.__dict__, "nt": min(g.nt, 1200)})
+            _, _, ul = api.forward(gg, m0, w, shot.src, rec[:1], return_state=True)
+            slab = ul[:16].cpu().numpy()
+        except Exception:
+            slab = None
+        v, cores, sample, _ = oracle_sample(shot, slab)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(args, shot, policy), "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "kernels": kernels,
+                "checkpoint_store": {"used_GiB": round(stats["used_bytes"] / 2**30, 2),
+                                     "compression_factor": round(stats["raw_bytes"] / max(1, stats["used_bytes"]), 2),
+                                     "checkpoints": stats["n_checkpoints"]},
+                "misfit": phi, "gradient_error": verify}
+        print(json.dumps(line), flush=True)
+    store.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fwi(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -164,14 +164,14 @@ int fwi_gradient_host(const fwi_geometry* g, const float* h_m, const float* h_wa
 size_t zfp_max_compressed_bytes(int nx, int ny, int nz);
 
 /* Compress d_in with tolerance atol > 0 into d_out (device, out_capacity
- * bytes).  *h_out_bytes = stream size.  FWI_ERR_CAPACITY (with *h_out_bytes =
+ * bytes, 8-byte aligned).  *h_out_bytes = stream size.  FWI_ERR_CAPACITY (with *h_out_bytes =
  * the size needed) if out_capacity is too small; FWI_ERR_NONFINITE if d_in
  * holds NaN or Inf.  Synchronises. */
 int zfp_compress_fixed_accuracy(const float* d_in, int nx, int ny, int nz, double atol,
                                 void* d_out, size_t out_capacity, size_t* h_out_bytes,
                                 void* stream);
 
-/* Decompress a stream of in_bytes bytes into d_out.  FWI_ERR_CORRUPT for a
+/* Decompress a stream of in_bytes bytes (d_in 8-byte aligned) into d_out.  FWI_ERR_CORRUPT for a
  * malformed stream (reads stay inside [d_in, d_in + in_bytes)), FWI_ERR_ARG
  * if its dimensions differ from nx, ny, nz.  Synchronises. */
 int zfp_decompress(const void* d_in, size_t in_bytes, float* d_out, int nx, int ny, int nz,
@@ -191,6 +191,16 @@ int fwi_dot_f64(const float* d_a, const float* d_b, size_t n, double* h_out, voi
 const char* fwi_status_string(int status);
 /* Number of kernels this library has launched since load (for accounting). */
 uint64_t fwi_kernel_launch_count(void);
+
+/* Per-kernel timing for roofline accounting.  While enabled, the library
+ * records a CUDA event pair on the launching stream around every launch of
+ * the timed classes (0 forward stencil, 1 adjoint stencil with imaging,
+ * 2 codec encode, 3 codec decode, 4 everything else); read returns, per
+ * class, the summed device milliseconds and launch count since the last
+ * reset (it waits for recorded events).  n must be >= 5. */
+int fwi_profile_enable(int on);
+int fwi_profile_reset(void);
+int fwi_profile_read(double* ms_out, uint64_t* launches_out, int n);
 
 #ifdef __cplusplus
 }

@@ -22,8 +22,10 @@ EXPORTS = [
     "fwi_ckpt_schedule", "fwi_ckpt_store_create", "fwi_ckpt_store_destroy", "fwi_ckpt_store_stats",
     "fwi_forward", "fwi_gradient", "fwi_gradient_host", "zfp_max_compressed_bytes",
     "zfp_compress_fixed_accuracy", "zfp_decompress", "fwi_misfit", "fwi_dot_f64",
-    "fwi_status_string", "fwi_kernel_launch_count",
+    "fwi_status_string", "fwi_kernel_launch_count", "fwi_profile_enable", "fwi_profile_reset",
+    "fwi_profile_read",
 ]
+KERNEL_CLASSES = ["stencil_forward", "stencil_adjoint_imaging", "zfp_encode", "zfp_decode", "other"]
 
 
 class FwiError(RuntimeError):
@@ -86,6 +88,9 @@ def load() -> C.CDLL:
         L.fwi_status_string.restype = C.c_char_p
         L.fwi_kernel_launch_count.argtypes = []
         L.fwi_kernel_launch_count.restype = C.c_uint64
+        L.fwi_profile_enable.argtypes = [C.c_int]
+        L.fwi_profile_reset.argtypes = []
+        L.fwi_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]
         _lib = L
         return L
 

@@ -63,6 +63,23 @@ def kernel_launch_count() -> int:
     return int(_lib.load().fwi_kernel_launch_count())
 
 
+def profile_enable(on: bool = True) -> None:
+    check("fwi_profile_enable", _lib.load().fwi_profile_enable(1 if on else 0))
+
+
+def profile_reset() -> None:
+    check("fwi_profile_reset", _lib.load().fwi_profile_reset())
+
+
+def profile_read() -> dict:
+    """{kernel class: (device ms, launches)} since the last reset."""
+    n = len(_lib.KERNEL_CLASSES)
+    ms = (C.c_double * n)()
+    cnt = (C.c_uint64 * n)()
+    check("fwi_profile_read", _lib.load().fwi_profile_read(ms, cnt, n))
+    return {k: (ms[i], int(cnt[i])) for i, k in enumerate(_lib.KERNEL_CLASSES)}
+
+
 def ckpt_schedule(nt: int, mode: int, k: int = 1, atol: float = 0.0):
     L = _lib.load()
     pol = _lib.Policy(mode, k, atol)

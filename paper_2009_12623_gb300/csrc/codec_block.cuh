@@ -1,0 +1,326 @@
+// Per-block arithmetic of the fixed-accuracy codec (one 4x4x4 block held in
+// 64 registers).  Written as __host__ __device__ functions so the CUDA kernels
+// in codec.cu and any host-side harness compile the very same code.
+#pragma once
+
+#include <stdint.h>
+#include <string.h>
+
+#ifdef __CUDACC__
+#define FZ_HD __host__ __device__ __forceinline__
+#else
+#define FZ_HD inline
+#endif
+
+namespace fwi {
+namespace zblock {
+
+constexpr int kS = 25;  // block-floating-point fraction bits
+constexpr int kG = 11;  // guard planes
+constexpr uint32_t kNB = 0xAAAAAAAAu;
+
+FZ_HD int clz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+  return __clz((int)x);
+#else
+  return x ? __builtin_clz(x) : 32;
+#endif
+}
+FZ_HD int clz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+FZ_HD int popc64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __popcll(x);
+#else
+  return __builtin_popcountll(x);
+#endif
+}
+// index of the lowest set bit (x != 0)
+FZ_HD int ctz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __ffsll((long long)x) - 1;
+#else
+  return __builtin_ctzll(x);
+#endif
+}
+FZ_HD float as_float(uint32_t u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+
+// ---- coefficient order (ascending total sequency, ties x-fastest) ----------
+struct PermTable {
+  int v[64];
+};
+FZ_HD constexpr PermTable make_perm() {
+  PermTable t{};
+  int n = 0;
+  for (int s = 0; s <= 9; ++s)
+    for (int idx = 0; idx < 64; ++idx)
+      if ((idx & 3) + ((idx >> 2) & 3) + (idx >> 4) == s) t.v[n++] = idx;
+  return t;
+}
+FZ_HD constexpr int perm_at(int p) { return make_perm().v[p]; }
+
+// ---- lifting transform on four values ---------------------------------------
+// (x0..x3) -> (S, D, d0, d1): pair differences and floor means, the same on
+// the two means, then the linear trend D/2 removed from both differences.
+FZ_HD void lift_fwd(int& x0, int& x1, int& x2, int& x3) {
+  int d0 = x1 - x0;
+  int s0 = x0 + (d0 >> 1);
+  int d1 = x3 - x2;
+  int s1 = x2 + (d1 >> 1);
+  int D = s1 - s0;
+  int S = s0 + (D >> 1);
+  int h = D >> 1;
+  x0 = S;
+  x1 = D;
+  x2 = d0 - h;
+  x3 = d1 - h;
+}
+FZ_HD void lift_inv(int& x0, int& x1, int& x2, int& x3) {
+  int h = x1 >> 1;
+  int d1 = x3 + h;
+  int d0 = x2 + h;
+  int s0 = x0 - h;
+  int s1 = x1 + s0;
+  int a2 = s1 - (d1 >> 1);
+  int a3 = d1 + a2;
+  int a0 = s0 - (d0 >> 1);
+  int a1 = d0 + a0;
+  x0 = a0;
+  x1 = a1;
+  x2 = a2;
+  x3 = a3;
+}
+FZ_HD void xform_fwd(int* q) {
+#pragma unroll
+  for (int l = 0; l < 16; ++l) lift_fwd(q[4 * l], q[4 * l + 1], q[4 * l + 2], q[4 * l + 3]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lift_fwd(q[i + 16 * k], q[i + 16 * k + 4], q[i + 16 * k + 8], q[i + 16 * k + 12]);
+#pragma unroll
+  for (int l = 0; l < 16; ++l) lift_fwd(q[l], q[l + 16], q[l + 32], q[l + 48]);
+}
+FZ_HD void xform_inv(int* q) {
+#pragma unroll
+  for (int l = 0; l < 16; ++l) lift_inv(q[l], q[l + 16], q[l + 32], q[l + 48]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lift_inv(q[i + 16 * k], q[i + 16 * k + 4], q[i + 16 * k + 8], q[i + 16 * k + 12]);
+#pragma unroll
+  for (int l = 0; l < 16; ++l) lift_inv(q[4 * l], q[4 * l + 1], q[4 * l + 2], q[4 * l + 3]);
+}
+
+// 32x32 bit-matrix transpose in registers: afterwards bit i of a[b] is what
+// was bit b of a[i] (recursive exchange of the off-diagonal blocks).
+FZ_HD void transpose32(uint32_t* a) {
+#pragma unroll
+  for (int lv = 0; lv < 5; ++lv) {
+    const int j = 16 >> lv;
+    const uint32_t m = lv == 0 ? 0x0000FFFFu : lv == 1 ? 0x00FF00FFu : lv == 2 ? 0x0F0F0F0Fu
+                     : lv == 3 ? 0x33333333u : 0x55555555u;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      if (k & j) continue;
+      const uint32_t t = ((a[k] >> j) ^ a[k + j]) & m;
+      a[k + j] ^= t;
+      a[k] ^= t << j;
+    }
+  }
+}
+
+FZ_HD int planes_for(int emax, int minexp) {
+  int p = emax - minexp + kG;
+  p = p < 0 ? 0 : (p > 32 ? 32 : p);
+  if (p == 30 || p == 31) p = 32;
+  return p;
+}
+
+FZ_HD uint64_t plane(const uint32_t* u, int b) {
+  return (uint64_t)u[b] | ((uint64_t)u[32 + b] << 32);
+}
+
+// FP32 bit patterns of a block -> 32 plane masks (u[b] | u[32+b] << 32 is
+// plane b), block exponent and coded-plane count.  Returns false (and codes
+// the block as zero) when the block holds NaN or Inf.
+FZ_HD bool quantise(uint32_t* u, int minexp, int& emax, int& planes) {
+  uint32_t maxbits = 0;
+#pragma unroll
+  for (int i = 0; i < 64; ++i) maxbits = maxbits > (u[i] & 0x7fffffffu) ? maxbits : (u[i] & 0x7fffffffu);
+  const bool finite = maxbits < 0x7f800000u;
+  if (!finite) maxbits = 0;
+  emax = 0;
+  planes = 0;
+  if (maxbits) {
+    const int E = (int)(maxbits >> 23);
+    const int e = E ? E - 126 : (32 - clz32(maxbits)) - 149;  // frexp exponent of max |x|
+    emax = e > -127 ? e : -127;
+    planes = planes_for(emax, minexp);
+  }
+  // q = trunc(x 2^(S - emax)) from the integer significand, exactly
+  int q[64];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) {
+    const uint32_t bits = u[i];
+    const int Eb = (int)((bits >> 23) & 0xffu);
+    const uint32_t M = Eb ? ((bits & 0x7fffffu) | 0x800000u) : (bits & 0x7fffffu);
+    const int sh = (Eb ? Eb : 1) - (150 - kS) - emax;
+    uint32_t mag = sh >= 0 ? (M << sh) : (sh > -32 ? (M >> (-sh)) : 0u);
+    if (!maxbits) mag = 0;
+    q[i] = (bits >> 31) ? -(int)mag : (int)mag;
+  }
+  xform_fwd(q);
+#pragma unroll
+  for (int p = 0; p < 64; ++p) u[p] = ((uint32_t)q[perm_at(p)] + kNB) ^ kNB;
+  transpose32(u);
+  transpose32(u + 32);
+  return finite;
+}
+
+// Exact number of bits the block codes to.
+FZ_HD int count_bits(const uint32_t* u, int planes) {
+  if (planes == 0) return 1;
+  int nbits = 9, n = 0;
+#pragma unroll
+  for (int b = 31; b >= 0; --b) {
+    if (b >= 32 - planes) {
+      const uint64_t m = plane(u, b);
+      const uint64_t r = n < 64 ? (m >> n) : 0ull;
+      const int nend = r ? 64 - clz64(m) : n;
+      nbits += nend + popc64(r) + (nend < 64 ? 1 : 0);
+      n = nend;
+    }
+  }
+  return nbits;
+}
+
+// Embedded bit-plane coding: per plane, the bits of the coefficients already
+// significant, then group tests each followed by the run up to the next
+// newly significant coefficient.  W provides put(value, nbits), 1..64 bits.
+template <class W>
+FZ_HD void emit(W& w, const uint32_t* u, int emax, int planes) {
+  if (planes == 0) {
+    w.put(0ull, 1);
+    return;
+  }
+  w.put(1ull | ((uint64_t)(emax + 127) << 1), 9);
+  int n = 0;
+#pragma unroll
+  for (int b = 31; b >= 0; --b) {
+    if (b >= 32 - planes) {
+      const uint64_t m = plane(u, b);
+      if (n > 0) w.put(n < 64 ? (m & ((1ull << n) - 1ull)) : m, n);
+      uint64_t r = n < 64 ? (m >> n) : 0ull;
+      while (n < 64) {
+        if (!r) {
+          w.put(0ull, 1);
+          break;
+        }
+        const int j = ctz64(r);
+        w.put(1ull, 1);
+        w.put(1ull << j, j + 1);
+        n += j + 1;
+        r = (j + 1 < 64) ? (r >> (j + 1)) : 0ull;
+      }
+    }
+  }
+}
+
+// Inverse of emit.  R provides pos/end (bit positions) and peek() (the next
+// 64 bits).  Returns false on a malformed block.
+template <class R>
+FZ_HD bool decode_planes(R& rd, int minexp, uint32_t* u, int& emax, int& planes) {
+#pragma unroll
+  for (int i = 0; i < 64; ++i) u[i] = 0u;
+  emax = 0;
+  planes = 0;
+  if (rd.pos + 1 > rd.end) return false;
+  const uint64_t hdr = rd.peek();
+  if (!(hdr & 1ull)) {
+    rd.pos += 1;
+    return true;
+  }
+  if (rd.pos + 9 > rd.end) return false;
+  emax = (int)((hdr >> 1) & 0xffull) - 127;
+  rd.pos += 9;
+  planes = planes_for(emax, minexp);
+  if (planes == 0) return false;
+  int n = 0;
+  bool ok = true;
+#pragma unroll
+  for (int b = 31; b >= 0; --b) {
+    if (b >= 32 - planes && ok) {
+      uint64_t m = 0ull;
+      if (n > 0) {
+        if (rd.pos + n > rd.end) {
+          ok = false;
+        } else {
+          const uint64_t v = rd.peek();
+          m = n < 64 ? (v & ((1ull << n) - 1ull)) : v;
+          rd.pos += n;
+        }
+      }
+      while (n < 64 && ok) {
+        if (rd.pos + 1 > rd.end) {
+          ok = false;
+          break;
+        }
+        const uint64_t t = rd.peek();
+        rd.pos += 1;
+        if (!(t & 1ull)) break;
+        const uint64_t pk = rd.peek();
+        const int j = pk ? ctz64(pk) : 64;
+        if (j >= 64 - n || rd.pos + j + 1 > rd.end) {
+          ok = false;
+          break;
+        }
+        rd.pos += j + 1;
+        m |= 1ull << (n + j);
+        n += j + 1;
+      }
+      u[b] = (uint32_t)m;
+      u[32 + b] = (uint32_t)(m >> 32);
+    }
+  }
+  return ok;
+}
+
+// Plane masks -> FP32 values: one rounding of q 2^(emax - S).
+FZ_HD void dequantise(uint32_t* u, int emax, int planes, float* v) {
+  if (planes == 0) {
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+    return;
+  }
+  transpose32(u);
+  transpose32(u + 32);
+  int q[64];
+#pragma unroll
+  for (int p = 0; p < 64; ++p) q[perm_at(p)] = (int)((u[p] ^ kNB) - kNB);
+  xform_inv(q);
+  const int k = emax - kS;
+  if (k >= -126) {
+    const float scale = as_float((uint32_t)(k + 127) << 23);
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = (float)q[i] * scale;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = (float)((double)q[i] * exp2((double)k));
+  }
+}
+
+}  // namespace zblock
+}  // namespace fwi

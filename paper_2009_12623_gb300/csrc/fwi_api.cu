@@ -1,0 +1,655 @@
+// C-ABI entry points of libfwi (declared in include/fwi.h): checkpoint store,
+// checkpoint schedule, forward modelling, the checkpointed gradient of
+// Kukreja et al. (Sec. 2 Eq. (2)-(4), Sec. 1.2-1.3, Fig. 1), the codec calls
+// and the FP64 reductions.  Host code here only validates arguments, owns
+// memory and sequences the kernels of stencil.cu and codec.cu on the caller's
+// stream; every arithmetic step of the path runs on the GPU.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fwi {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---- per-kernel timing: event pairs recorded around launches ---------------
+namespace {
+struct ProfSlot {
+  int cls;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfSlot> g_prof_slots;   // recorded, not yet read
+std::vector<cudaEvent_t> g_prof_free;  // reusable events
+double g_prof_ms[KC_COUNT] = {0};
+unsigned long long g_prof_n[KC_COUNT] = {0};
+
+cudaEvent_t prof_event() {
+  if (!g_prof_free.empty()) {
+    cudaEvent_t e = g_prof_free.back();
+    g_prof_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Fold completed slots into the totals (caller holds the lock).
+void prof_drain(bool wait) {
+  size_t keep = 0;
+  for (size_t i = 0; i < g_prof_slots.size(); ++i) {
+    ProfSlot& p = g_prof_slots[i];
+    if (wait) cudaEventSynchronize(p.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_prof_ms[p.cls] += ms;
+      g_prof_n[p.cls] += 1;
+      g_prof_free.push_back(p.a);
+      g_prof_free.push_back(p.b);
+    } else {
+      cudaGetLastError();
+      g_prof_slots[keep++] = p;
+    }
+  }
+  g_prof_slots.resize(keep);
+}
+}  // namespace
+
+int prof_begin(int cls, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return -1;
+  if (g_prof_slots.size() > 4096) prof_drain(false);
+  cudaEvent_t a = prof_event(), b = prof_event();
+  if (!a || !b) return -1;
+  cudaEventRecord(a, s);
+  g_prof_slots.push_back(ProfSlot{cls, a, b});
+  return (int)g_prof_slots.size() - 1;
+}
+
+void prof_end(int slot, cudaStream_t s) {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot < (int)g_prof_slots.size()) cudaEventRecord(g_prof_slots[slot].b, s);
+}
+
+int status_from_flags(int f) {
+  if (f & ST_CAPACITY) return FWI_ERR_CAPACITY;
+  if (f & ST_NONFINITE) return FWI_ERR_NONFINITE;
+  if (f & ST_CORRUPT) return FWI_ERR_CORRUPT;
+  if (f & ST_TIMEOUT) return FWI_ERR_TIMEOUT;
+  return FWI_OK;
+}
+
+namespace {
+
+// 8th-order central second-difference weights (times h^2).
+const double kC[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+
+// Stream-ordered allocations released when the scope ends.
+struct Pool {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  bool failed = false;
+  explicit Pool(cudaStream_t st) : s(st) {}
+  template <class T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMallocAsync(&p, n * sizeof(T), s) != cudaSuccess) {
+      failed = true;
+      cudaGetLastError();
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Pool() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+bool geometry_ok(const fwi_geometry* g) {
+  return g && g->nx > 0 && g->ny > 0 && g->nz > 0 && g->nt >= 0 && g->h > 0 && g->dt > 0 &&
+         g->nbl >= 0 && (g->nbl == 0 || (g->sponge_R > 0 && g->sponge_R < 1 && g->vmax > 0)) &&
+         (long)g->nx * g->ny * g->nz < (1L << 40);
+}
+
+int minexp_of(double atol) {
+  int e;
+  frexp(atol, &e);
+  return e - 1;
+}
+
+#define CK(x)                          \
+  do {                                 \
+    if ((x) != cudaSuccess) {          \
+      cudaGetLastError();              \
+      return FWI_ERR_CUDA;             \
+    }                                  \
+  } while (0)
+
+// Everything the sweeps need on the device.
+struct Sweep {
+  Grid G;
+  StencilParams sp;
+  float* d_wavelet = nullptr;
+  long src = -1;
+  long* rec_cell = nullptr;
+  float* rec_fac = nullptr;
+  int* d_status = nullptr;
+};
+
+int setup_sweep(Pool& pool, const fwi_geometry* g, const float* d_m, const float* h_wavelet,
+                int si, int sj, int sk, const int* d_rec_ijk, int nrec, Sweep& sw) {
+  cudaStream_t s = pool.s;
+  sw.G = Grid{g->nx, g->ny, g->nz, round_up(g->nx, 4)};
+  sw.sp.g = sw.G;
+  for (int r = 0; r < 5; ++r) sw.sp.c[r] = (float)(kC[r] / (g->h * g->h));
+  sw.sp.dt = (float)g->dt;
+  float* b = pool.get<float>(sw.G.cells());
+  float* sx = pool.get<float>(g->nx);
+  float* sy = pool.get<float>(g->ny);
+  float* sz = pool.get<float>(g->nz);
+  sw.d_wavelet = pool.get<float>(g->nt > 0 ? g->nt : 1);
+  sw.rec_cell = pool.get<long>(nrec > 0 ? nrec : 1);
+  sw.rec_fac = pool.get<float>(nrec > 0 ? nrec : 1);
+  sw.d_status = pool.get<int>(1);
+  if (pool.failed) return FWI_ERR_NOMEM;
+  sw.sp.b = b;
+  sw.sp.sx = sx;
+  sw.sp.sy = sy;
+  sw.sp.sz = sz;
+  sw.sp.status = sw.d_status;
+  CK(cudaMemsetAsync(sw.d_status, 0, sizeof(int), s));
+  if (g->nt > 0) CK(cudaMemcpyAsync(sw.d_wavelet, h_wavelet, sizeof(float) * g->nt, cudaMemcpyHostToDevice, s));
+  CK(setup_model_launch(d_m, sw.G, (float)g->dt, b, sw.d_status, s));
+  CK(setup_profiles_launch(sw.G, g->nbl, g->h, g->vmax, g->sponge_R, g->dt, sx, sy, sz, s));
+  CK(rec_cells_launch(d_rec_ijk, nrec, sw.G, sw.rec_cell, sw.d_status, s));
+  CK(rec_fac_launch(sw.sp, sw.rec_cell, nrec, sw.rec_fac, s));
+  sw.src = (long)si + (long)sw.G.pitch * ((long)sj + (long)g->ny * sk);
+  return FWI_OK;
+}
+
+bool in_grid(const fwi_geometry* g, int i, int j, int k) {
+  return i >= 0 && j >= 0 && k >= 0 && i < g->nx && j < g->ny && k < g->nz;
+}
+
+// Schedule generator: the event list of Sec. 1.2 for the two policies.
+struct Sched {
+  std::vector<fwi_action> a;
+  void add(int kind, int step, int arg) { a.push_back(fwi_action{kind, step, arg}); }
+};
+
+int make_schedule(int nt, const fwi_ckpt_policy* pol, Sched& out) {
+  if (!pol || nt < 0) return FWI_ERR_ARG;
+  if (pol->mode == FWI_CKPT_FULL) {
+    for (int s = 0; s < nt; ++s) {
+      out.add(FWI_ACT_ADVANCE, s, 0);
+      out.add(FWI_ACT_STORE, s + 1, 1);
+    }
+    for (int k = nt; k > 0; --k) {
+      out.add(FWI_ACT_RESTORE, k, 1);
+      out.add(FWI_ACT_ADJOINT, k, 0);
+    }
+    return FWI_OK;
+  }
+  if (pol->mode == FWI_CKPT_EVERY_K) {
+    const int K = pol->k_or_snaps;
+    if (K < 1) return FWI_ERR_ARG;
+    out.add(FWI_ACT_STORE, 0, 2);
+    for (int s = 1; s <= nt; ++s) {
+      out.add(FWI_ACT_ADVANCE, s - 1, 0);
+      if (s % K == 0) out.add(FWI_ACT_STORE, s, 2);
+    }
+    // segments [c, min(c+K-1, nt)] from the last checkpoint back to 0
+    for (int c = nt - nt % K; c >= 0; c -= K) {
+      const int last = std::min(c + K - 1, nt);
+      const int first = std::max(c, 1);
+      if (last < first) continue;
+      out.add(FWI_ACT_RESTORE, c, 2);
+      for (int s = c; s < last; ++s) out.add(FWI_ACT_RECOMPUTE, s, 0);
+      for (int k = last; k >= first; --k) out.add(FWI_ACT_ADJOINT, k, 0);
+    }
+    return FWI_OK;
+  }
+  return FWI_ERR_ARG;
+}
+
+// Offset bookkeeping for compressed slots: the next slot starts where the
+// previous one ended (256-byte aligned).  Runs on the device so that no host
+// synchronisation is needed between checkpoints.
+__global__ void k_slot_offset(unsigned long long* off, const unsigned long long* size, int j) {
+  off[j] = j == 0 ? 0ull : off[j - 1] + ((size[j - 1] + 255ull) & ~255ull);
+}
+__global__ void k_end_offset(const unsigned long long* off, const unsigned long long* size, int n,
+                             unsigned long long* end) {
+  *end = n == 0 ? 0ull : off[n - 1] + ((size[n - 1] + 255ull) & ~255ull);
+}
+
+}  // namespace
+}  // namespace fwi
+
+using namespace fwi;
+
+struct fwi_ckpt_store {
+  uint8_t* arena = nullptr;
+  size_t capacity = 0;
+  fwi_store_stats stats{};
+};
+
+extern "C" {
+
+const char* fwi_status_string(int st) {
+  switch (st) {
+    case FWI_OK: return "ok";
+    case FWI_ERR_ARG: return "invalid argument";
+    case FWI_ERR_CAPACITY: return "capacity exceeded";
+    case FWI_ERR_CORRUPT: return "corrupt compressed stream";
+    case FWI_ERR_NONFINITE: return "non-finite value";
+    case FWI_ERR_CUDA: return "CUDA runtime error";
+    case FWI_ERR_TIMEOUT: return "device wait timed out";
+    case FWI_ERR_NOMEM: return "device allocation failed";
+    default: return "unknown status";
+  }
+}
+
+uint64_t fwi_kernel_launch_count(void) { return g_launches.load(); }
+
+int fwi_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return FWI_OK;
+}
+
+int fwi_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain(true);
+  for (int i = 0; i < KC_COUNT; ++i) {
+    g_prof_ms[i] = 0.0;
+    g_prof_n[i] = 0;
+  }
+  return FWI_OK;
+}
+
+int fwi_profile_read(double* ms_out, uint64_t* launches_out, int n) {
+  if (!ms_out || !launches_out || n < KC_COUNT) return FWI_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain(true);
+  for (int i = 0; i < KC_COUNT; ++i) {
+    ms_out[i] = g_prof_ms[i];
+    launches_out[i] = g_prof_n[i];
+  }
+  return FWI_OK;
+}
+
+int fwi_ckpt_schedule(int nt, const fwi_ckpt_policy* pol, fwi_action* out, size_t cap,
+                      size_t* n_out) {
+  if (!n_out) return FWI_ERR_ARG;
+  Sched sc;
+  int st = make_schedule(nt, pol, sc);
+  if (st) return st;
+  *n_out = sc.a.size();
+  if (!out || cap < sc.a.size()) return FWI_ERR_CAPACITY;
+  memcpy(out, sc.a.data(), sizeof(fwi_action) * sc.a.size());
+  return FWI_OK;
+}
+
+int fwi_ckpt_store_create(size_t capacity_bytes, fwi_ckpt_store** out) {
+  if (!out || capacity_bytes == 0) return FWI_ERR_ARG;
+  fwi_ckpt_store* st = new fwi_ckpt_store();
+  if (cudaMalloc(&st->arena, capacity_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete st;
+    return FWI_ERR_NOMEM;
+  }
+  st->capacity = capacity_bytes;
+  st->stats.capacity_bytes = capacity_bytes;
+  *out = st;
+  return FWI_OK;
+}
+
+int fwi_ckpt_store_destroy(fwi_ckpt_store* st) {
+  if (!st) return FWI_ERR_ARG;
+  if (st->arena) cudaFree(st->arena);
+  delete st;
+  return FWI_OK;
+}
+
+int fwi_ckpt_store_stats(const fwi_ckpt_store* st, fwi_store_stats* out) {
+  if (!st || !out) return FWI_ERR_ARG;
+  *out = st->stats;
+  return FWI_OK;
+}
+
+int fwi_forward(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
+                int src_j, int src_k, const int* d_rec_ijk, int nrec, float* d_rec_out,
+                const float* d_u_prev_init, const float* d_u_cur_init, float* d_u_prev_out,
+                float* d_u_last_out, void* stream) {
+  if (!geometry_ok(g) || !d_m || (g->nt > 0 && !h_wavelet) || nrec < 0 ||
+      (nrec > 0 && (!d_rec_ijk || !d_rec_out)) || !in_grid(g, src_i, src_j, src_k))
+    return FWI_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Pool pool(s);
+  Sweep sw;
+  int st = setup_sweep(pool, g, d_m, h_wavelet, src_i, src_j, src_k, d_rec_ijk, nrec, sw);
+  if (st) return st;
+  float* prev = pool.get<float>(sw.G.cells());
+  float* cur = pool.get<float>(sw.G.cells());
+  if (pool.failed) return FWI_ERR_NOMEM;
+  CK(cudaMemsetAsync(prev, 0, sw.G.cells() * 4, s));
+  CK(cudaMemsetAsync(cur, 0, sw.G.cells() * 4, s));
+  if (d_u_prev_init) CK(unpack_launch(d_u_prev_init, sw.G, prev, s));
+  if (d_u_cur_init) CK(unpack_launch(d_u_cur_init, sw.G, cur, s));
+  for (int n = 0; n < g->nt; ++n) {
+    CK(stencil_step_launch(sw.sp, cur, prev, prev, sw.src, sw.d_wavelet, n, s));
+    std::swap(prev, cur);
+    CK(gather_launch(cur, sw.rec_cell, nrec, d_rec_out + (size_t)n * nrec, s));
+  }
+  if (d_u_prev_out) CK(pack_launch(prev, sw.G, d_u_prev_out, s));
+  if (d_u_last_out) CK(pack_launch(cur, sw.G, d_u_last_out, s));
+  int flags = 0;
+  CK(cudaMemcpyAsync(&flags, sw.d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flags & ST_CORRUPT) return FWI_ERR_ARG;  // receiver outside the grid
+  return status_from_flags(flags);
+}
+
+int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
+                 int src_j, int src_k, const int* d_rec_ijk, int nrec, const float* d_obs,
+                 float* d_grad, double* h_misfit, fwi_ckpt_store* store,
+                 const fwi_ckpt_policy* pol, void* stream) {
+  if (!geometry_ok(g) || !d_m || (g->nt > 0 && !h_wavelet) || nrec < 0 ||
+      (nrec > 0 && (!d_rec_ijk || !d_obs)) || !d_grad || !h_misfit || !store || !pol ||
+      !in_grid(g, src_i, src_j, src_k))
+    return FWI_ERR_ARG;
+  Sched sc;
+  int st = make_schedule(g->nt, pol, sc);
+  if (st) return st;
+  const bool lossy = pol->atol > 0.0;
+  if (lossy && !isfinite(pol->atol)) return FWI_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Pool pool(s);
+  Sweep sw;
+  st = setup_sweep(pool, g, d_m, h_wavelet, src_i, src_j, src_k, d_rec_ijk, nrec, sw);
+  if (st) return st;
+  const Grid G = sw.G;
+  const size_t fbytes = G.cells() * sizeof(float);
+  const int N = g->nt;
+
+  // slot numbering: (step, level) -> slot; level 1 = u^step, 0 = u^{step-1}
+  std::map<std::pair<int, int>, int> slot;
+  for (const fwi_action& a : sc.a)
+    if (a.kind == FWI_ACT_STORE && a.step > 0) {
+      const int j = (int)slot.size();
+      slot[{a.step, 1}] = j;
+      if (a.arg == 2) slot[{a.step, 0}] = j + 1;
+    }
+  const int nslots = (int)slot.size();
+  const size_t raw_slot = (fbytes + 255) / 256 * 256;
+  store->stats = fwi_store_stats{store->capacity, 0, (size_t)nslots * (size_t)G.nx * G.ny * G.nz * 4,
+                                 nslots, 0};
+  if (!lossy && (size_t)nslots * raw_slot > store->capacity) {
+    store->stats.used_bytes = (size_t)nslots * raw_slot;
+    store->stats.overflowed = 1;
+    return FWI_ERR_CAPACITY;
+  }
+
+  float* fprev = pool.get<float>(G.cells());
+  float* fcur = pool.get<float>(G.cells());
+  float* lnext = pool.get<float>(G.cells());
+  float* lcur = pool.get<float>(G.cells());
+  float* gacc = pool.get<float>(G.cells());
+  float* dsim = pool.get<float>((size_t)N * (nrec > 0 ? nrec : 1));
+  double* d_phi = pool.get<double>(1);
+  double* d_part = pool.get<double>(reduce_scratch_doubles());
+  unsigned long long* offs = pool.get<unsigned long long>(nslots + 1);
+  unsigned long long* sizes = pool.get<unsigned long long>(nslots + 1);
+  unsigned long long* scratch = pool.get<unsigned long long>(zfp_encode_scratch_words(G.nx, G.ny, G.nz));
+  const int K = pol->mode == FWI_CKPT_EVERY_K ? pol->k_or_snaps : 1;
+  std::vector<float*> ring(K, nullptr);
+  for (int i = 0; i < K; ++i) ring[i] = pool.get<float>(G.cells());
+  float* rprev = pool.get<float>(G.cells());
+  if (pool.failed) return FWI_ERR_NOMEM;
+  for (float* f : {fprev, fcur, lnext, lcur, gacc, rprev}) CK(cudaMemsetAsync(f, 0, fbytes, s));
+  CK(cudaMemsetAsync(d_phi, 0, sizeof(double), s));
+  CK(cudaMemsetAsync(sizes, 0, sizeof(unsigned long long) * (nslots + 1), s));
+  const int minexp = lossy ? minexp_of(pol->atol) : 0;
+
+  auto store_field = [&](const float* f, int j) -> int {
+    if (lossy) {
+      k_slot_offset<<<1, 1, 0, s>>>(offs, sizes, j);
+      count_launch();
+      CK(cudaGetLastError());
+      CK(zfp_encode_launch(f, G, minexp, store->arena, offs + j, store->capacity, sizes + j,
+                           sw.d_status, scratch, s));
+    } else {
+      CK(cudaMemcpyAsync(store->arena + (size_t)j * raw_slot, f, fbytes, cudaMemcpyDeviceToDevice, s));
+    }
+    return FWI_OK;
+  };
+  auto load_field = [&](int j, float* f) -> int {
+    if (lossy) {
+      CK(zfp_decode_launch(store->arena, offs + j, store->capacity, f, G, sw.d_status, s));
+    } else {
+      CK(cudaMemcpyAsync(f, store->arena + (size_t)j * raw_slot, fbytes, cudaMemcpyDeviceToDevice, s));
+    }
+    return FWI_OK;
+  };
+
+  std::vector<float*> avail(N + 2, nullptr);
+  int seg_c = 0;
+  bool resid_ready = false;
+  for (const fwi_action& a : sc.a) {
+    switch (a.kind) {
+      case FWI_ACT_ADVANCE:
+        CK(stencil_step_launch(sw.sp, fcur, fprev, fprev, sw.src, sw.d_wavelet, a.step, s));
+        std::swap(fprev, fcur);
+        CK(gather_launch(fcur, sw.rec_cell, nrec, dsim + (size_t)a.step * nrec, s));
+        break;
+      case FWI_ACT_STORE:
+        if (a.step > 0) {
+          if ((st = store_field(fcur, slot[{a.step, 1}]))) return st;
+          if (a.arg == 2 && (st = store_field(fprev, slot[{a.step, 0}]))) return st;
+        }
+        break;
+      case FWI_ACT_RESTORE:
+        if (a.arg == 1) {  // full history: u^k into the decode buffer
+          if ((st = load_field(slot[{a.step, 1}], rprev))) return st;
+          avail[a.step] = rprev;
+        } else {           // state pair at the segment start
+          seg_c = a.step;
+          if (a.step == 0) {
+            CK(cudaMemsetAsync(rprev, 0, fbytes, s));
+            CK(cudaMemsetAsync(ring[0], 0, fbytes, s));
+          } else {
+            if ((st = load_field(slot[{a.step, 0}], rprev))) return st;
+            if ((st = load_field(slot[{a.step, 1}], ring[0]))) return st;
+          }
+          avail[a.step] = ring[0];
+        }
+        break;
+      case FWI_ACT_RECOMPUTE: {
+        const int i = a.step - seg_c;
+        const float* prev = i == 0 ? rprev : ring[i - 1];
+        CK(stencil_step_launch(sw.sp, ring[i], prev, ring[i + 1], sw.src, sw.d_wavelet, a.step, s));
+        avail[a.step + 1] = ring[i + 1];
+        break;
+      }
+      case FWI_ACT_ADJOINT: {
+        const int k = a.step;
+        if (!resid_ready) {
+          CK(misfit_launch(dsim, d_obs, (size_t)N * nrec, dsim, d_phi, d_part, s));
+          resid_ready = true;
+        }
+        if (!avail[k]) return FWI_ERR_ARG;
+        CK(stencil_adjoint_launch(sw.sp, lcur, lnext, lnext, avail[k], gacc, s));
+        CK(inject_adjoint_launch(sw.sp, sw.rec_cell, sw.rec_fac, nrec, dsim + (size_t)(k - 1) * nrec,
+                                 lnext, avail[k], gacc, s));
+        std::swap(lcur, lnext);  // lcur = l_{k-1}, lnext = l_k
+        avail[k] = nullptr;
+        break;
+      }
+      default:
+        return FWI_ERR_ARG;
+    }
+  }
+  unsigned long long* d_end = sizes + nslots;
+  if (lossy) {
+    k_end_offset<<<1, 1, 0, s>>>(offs, sizes, nslots, d_end);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  int flags = 0;
+  double phi = 0.0;
+  unsigned long long used = lossy ? 0ull : (unsigned long long)nslots * raw_slot;
+  CK(cudaMemcpyAsync(&flags, sw.d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&phi, d_phi, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (lossy) CK(cudaMemcpyAsync(&used, d_end, sizeof(used), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  store->stats.used_bytes = (size_t)used;
+  store->stats.overflowed = (flags & ST_CAPACITY) ? 1 : 0;
+  if (flags) {
+    if ((flags & ST_CORRUPT) && !(flags & ST_CAPACITY) && !(flags & ST_NONFINITE)) {
+      // an out-of-range receiver also raises this flag during setup
+      return FWI_ERR_ARG;
+    }
+    return status_from_flags(flags);
+  }
+  CK(unpack_add_launch(gacc, G, d_grad, s));
+  CK(cudaStreamSynchronize(s));
+  *h_misfit = phi;
+  return FWI_OK;
+}
+
+int fwi_gradient_host(const fwi_geometry* g, const float* h_m, const float* h_wavelet, int src_i,
+                      int src_j, int src_k, const int* h_rec_ijk, int nrec, const float* h_obs,
+                      float* h_grad, double* h_misfit, fwi_ckpt_store* st,
+                      const fwi_ckpt_policy* pol, void* stream) {
+  if (!geometry_ok(g) || !h_m || !h_grad || nrec < 0 || (nrec > 0 && (!h_rec_ijk || !h_obs)))
+    return FWI_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t C = (size_t)g->nx * g->ny * g->nz;
+  const size_t nobs = (size_t)g->nt * nrec;
+  float *dm = nullptr, *dobs = nullptr, *dgrad = nullptr;
+  int* drec = nullptr;
+  int rc = FWI_OK;
+  if (cudaMallocAsync(&dm, C * 4, s) != cudaSuccess || cudaMallocAsync(&dgrad, C * 4, s) != cudaSuccess ||
+      cudaMallocAsync(&dobs, (nobs ? nobs : 1) * 4, s) != cudaSuccess ||
+      cudaMallocAsync(&drec, (nrec ? nrec : 1) * 12, s) != cudaSuccess) {
+    cudaGetLastError();
+    rc = FWI_ERR_NOMEM;
+  }
+  if (!rc && (cudaMemcpyAsync(dm, h_m, C * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+              cudaMemcpyAsync(dgrad, h_grad, C * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+              (nobs && cudaMemcpyAsync(dobs, h_obs, nobs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+              (nrec && cudaMemcpyAsync(drec, h_rec_ijk, (size_t)nrec * 12, cudaMemcpyHostToDevice, s) != cudaSuccess)))
+    rc = FWI_ERR_CUDA;
+  if (!rc) rc = fwi_gradient(g, dm, h_wavelet, src_i, src_j, src_k, drec, nrec, dobs, dgrad, h_misfit,
+                             st, pol, stream);
+  if (!rc && (cudaMemcpyAsync(h_grad, dgrad, C * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess))
+    rc = FWI_ERR_CUDA;
+  for (void* p : {(void*)dm, (void*)dobs, (void*)dgrad, (void*)drec})
+    if (p) cudaFreeAsync(p, s);
+  cudaStreamSynchronize(s);
+  cudaGetLastError();
+  return rc;
+}
+
+size_t zfp_max_compressed_bytes(int nx, int ny, int nz) {
+  if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
+  return zlayout(nx, ny, nz).max_bytes;
+}
+
+int zfp_compress_fixed_accuracy(const float* d_in, int nx, int ny, int nz, double atol, void* d_out,
+                                size_t out_capacity, size_t* h_out_bytes, void* stream) {
+  if (!d_in || !d_out || !h_out_bytes || nx <= 0 || ny <= 0 || nz <= 0 || !(atol > 0.0) ||
+      !isfinite(atol) || ((uintptr_t)d_out & 7) || ((uintptr_t)d_in & 3))
+    return FWI_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Pool pool(s);
+  const size_t words = zfp_encode_scratch_words(nx, ny, nz);
+  unsigned long long* scratch = pool.get<unsigned long long>(words + 1);
+  int* d_status = pool.get<int>(1);
+  if (pool.failed) return FWI_ERR_NOMEM;
+  unsigned long long* d_size = scratch + words;
+  CK(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+  CK(zfp_encode_launch(d_in, Grid{nx, ny, nz, nx}, minexp_of(atol), (uint8_t*)d_out, nullptr,
+                       out_capacity, d_size, d_status, scratch, s));
+  unsigned long long size = 0;
+  int flags = 0;
+  CK(cudaMemcpyAsync(&size, d_size, sizeof(size), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&flags, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *h_out_bytes = (size_t)size;
+  return status_from_flags(flags);
+}
+
+int zfp_decompress(const void* d_in, size_t in_bytes, float* d_out, int nx, int ny, int nz,
+                   void* stream) {
+  if (!d_in || !d_out || nx <= 0 || ny <= 0 || nz <= 0 || ((uintptr_t)d_in & 7) ||
+      ((uintptr_t)d_out & 3))
+    return FWI_ERR_ARG;
+  if (in_bytes < 64) return FWI_ERR_CORRUPT;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t hdr[16];
+  CK(cudaMemcpyAsync(hdr, d_in, 64, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hdr[0] != ZC_MAGIC || hdr[1] != ZC_VERSION) return FWI_ERR_CORRUPT;
+  if ((int)hdr[2] != nx || (int)hdr[3] != ny || (int)hdr[4] != nz) return FWI_ERR_ARG;
+  Pool pool(s);
+  int* d_status = pool.get<int>(1);
+  if (pool.failed) return FWI_ERR_NOMEM;
+  CK(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+  CK(zfp_decode_launch((const uint8_t*)d_in, nullptr, in_bytes, d_out, Grid{nx, ny, nz, nx}, d_status, s));
+  int flags = 0;
+  CK(cudaMemcpyAsync(&flags, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return status_from_flags(flags);
+}
+
+int fwi_misfit(const float* d_sim, const float* d_obs, size_t n, float* d_resid, double* h_misfit,
+               void* stream) {
+  if (!h_misfit || (n > 0 && (!d_sim || !d_obs || !d_resid))) return FWI_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Pool pool(s);
+  double* acc = pool.get<double>(1);
+  double* part = pool.get<double>(reduce_scratch_doubles());
+  if (pool.failed) return FWI_ERR_NOMEM;
+  CK(cudaMemsetAsync(acc, 0, sizeof(double), s));
+  CK(misfit_launch(d_sim, d_obs, n, d_resid, acc, part, s));
+  CK(cudaMemcpyAsync(h_misfit, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return FWI_OK;
+}
+
+int fwi_dot_f64(const float* d_a, const float* d_b, size_t n, double* h_out, void* stream) {
+  if (!h_out || (n > 0 && (!d_a || !d_b))) return FWI_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Pool pool(s);
+  double* acc = pool.get<double>(1);
+  double* part = pool.get<double>(reduce_scratch_doubles());
+  if (pool.failed) return FWI_ERR_NOMEM;
+  CK(cudaMemsetAsync(acc, 0, sizeof(double), s));
+  CK(dot_launch(d_a, d_b, n, acc, part, s));
+  CK(cudaMemcpyAsync(h_out, acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return FWI_OK;
+}
+
+}  // extern "C"

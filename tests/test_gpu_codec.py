@@ -1,0 +1,114 @@
+"""GPU codec parity with the oracle: compressed streams bit-exact, decoded
+values bit-exact (Sec. 1.3 fixed-accuracy compression of checkpoints)."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _field(shape, seed, kind="lognormal"):
+    rng = np.random.default_rng(seed)
+    if kind == "lognormal":
+        return (rng.normal(size=shape) * np.exp(2 * rng.normal(size=shape))).astype(np.float32)
+    if kind == "smooth":
+        z, y, x = np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+        return (np.sin(0.3 * x) * np.cos(0.2 * y + 0.1 * z) * 0.7).astype(np.float32)
+    raise ValueError(kind)
+
+
+def _gpu_compress(cuda, f, atol):
+    from paper_2009_12623_gb300 import api
+    return api.zfp_compress(torch.from_numpy(f).to(cuda), atol).cpu().numpy().tobytes()
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 5, 7), (9, 10, 11), (16, 16, 16), (13, 4, 17),
+                                   (37, 29, 23), (8, 64, 129)])
+@pytest.mark.parametrize("atol", [1e-1, 1e-3, 1e-6])
+def test_stream_bitexact(cuda, oracle, shape, atol):
+    from paper_2009_12623_gb300 import api
+    for kind in ("lognormal", "smooth"):
+        f = _field(shape, sum(shape), kind)
+        ref = oracle.zfp_compress(f, atol)
+        got = _gpu_compress(cuda, f, atol)
+        assert len(got) == len(ref)
+        assert got == ref
+        dec = api.zfp_decompress(torch.frombuffer(bytearray(got), dtype=torch.uint8).to(cuda), shape)
+        assert np.array_equal(dec.cpu().numpy(), oracle.zfp_decompress(ref, shape))
+
+
+def test_edge_values_bitexact(cuda, oracle):
+    shape = (8, 12, 16)
+    rng = np.random.default_rng(5)
+    f = rng.normal(size=shape).astype(np.float32)
+    f[0] = 0.0
+    f[1] = np.ldexp(rng.normal(size=shape[1:]), -140).astype(np.float32)   # subnormals
+    f[2] = np.ldexp(rng.normal(size=shape[1:]), 120).astype(np.float32)    # huge
+    f[3, :, ::2] = -0.0
+    f[4] = 1e-38
+    for atol in (1e-30, 1e-3, 1e30):
+        ref = oracle.zfp_compress(f, atol)
+        assert _gpu_compress(cuda, f, atol) == ref
+
+
+def test_nonfinite_rejected(cuda):
+    from paper_2009_12623_gb300 import api, _lib
+    f = torch.zeros((8, 8, 8), device=cuda)
+    f[3, 4, 5] = float("nan")
+    st, _, _ = api.zfp_compress_status(f, 1e-3, api.zfp_max_compressed_bytes(8, 8, 8))
+    assert st == _lib.FWI_ERR_NONFINITE
+    f[3, 4, 5] = float("inf")
+    st, _, _ = api.zfp_compress_status(f, 1e-3, api.zfp_max_compressed_bytes(8, 8, 8))
+    assert st == _lib.FWI_ERR_NONFINITE
+
+
+def test_capacity_reports_needed_bytes(cuda, oracle):
+    from paper_2009_12623_gb300 import api, _lib
+    f = _field((20, 21, 22), 1)
+    ref = oracle.zfp_compress(f, 1e-4)
+    t = torch.from_numpy(f).to(cuda)
+    for cap in (0, 64, len(ref) // 2, len(ref) - 8):
+        st, n, _ = api.zfp_compress_status(t, 1e-4, cap)
+        assert st == _lib.FWI_ERR_CAPACITY and n == len(ref)
+    st, n, out = api.zfp_compress_status(t, 1e-4, len(ref))
+    assert st == 0 and out[:n].cpu().numpy().tobytes() == ref
+
+
+def test_corrupt_streams_rejected(cuda, oracle):
+    from paper_2009_12623_gb300 import api, _lib
+    shape = (12, 9, 10)
+    f = _field(shape, 2)
+    ref = bytearray(oracle.zfp_compress(f, 1e-3))
+    dev = torch.frombuffer(ref, dtype=torch.uint8).to(cuda)
+    for cut in (64, 100, len(ref) - 8):
+        st, _ = api.zfp_decompress_status(dev, cut, shape)
+        assert st == _lib.FWI_ERR_CORRUPT
+    lt = 64 + 8 * int(np.frombuffer(bytes(ref[36:40]), np.uint32)[0])
+    for pos in (0, 40, lt, lt + 1, len(ref) - 3):
+        bad = bytearray(ref)
+        bad[pos] ^= 0x5
+        st, _ = api.zfp_decompress_status(torch.frombuffer(bad, dtype=torch.uint8).to(cuda), len(bad), shape)
+        ost, _ = oracle.zfp_decompress_status(bytes(bad), shape)
+        assert (st != 0) == (ost != 0), (pos, st, ost)
+    # random garbage payload never faults
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        bad = bytearray(ref)
+        p0 = lt + 2 * 100
+        bad[p0:] = rng.integers(0, 256, len(bad) - p0, dtype=np.uint8).tobytes()
+        st, _ = api.zfp_decompress_status(torch.frombuffer(bad, dtype=torch.uint8).to(cuda), len(bad), shape)
+        assert st in (0, _lib.FWI_ERR_CORRUPT)
+
+
+def test_shells_field_bitexact_and_bounded(cuda, oracle):
+    """Codec benchmark workload (512^3 shell snapshot), reduced to 256^3 here;
+    the full 512^3 case runs in the full-size test module."""
+    from paper_2009_12623_gb300 import api, synth
+    f = synth.shells_field(256, seed=0, rmin=25, rmax=100)
+    t = torch.from_numpy(f).to(cuda)
+    for atol in (1e-2, 1e-4):
+        got = api.zfp_compress(t, atol)
+        ref = oracle.zfp_compress(f, atol)
+        assert got.cpu().numpy().tobytes() == ref
+        dec = api.zfp_decompress(got.clone(), f.shape)
+        assert (dec - t).abs().max().item() < atol

@@ -1,0 +1,218 @@
+"""GPU forward sweep, checkpointed gradient and reductions vs the FP64 oracle
+(Sec. 2 Eq. (2)-(4); Sec. 1.2-1.3).  Tolerance: FP32 fields within 1e-4
+relative L2 of the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _og(oracle, g):
+    return oracle.geometry(g.nx, g.ny, g.nz, g.h, g.dt, g.nt, g.nbl, g.sponge_R, g.vmax)
+
+
+def _small_shot(nx=37, ny=29, nz=23, nt=80, nbl=5):
+    from paper_2009_12623_gb300 import synth
+    from paper_2009_12623_gb300.api import Geometry
+    rng = np.random.default_rng(11)
+    z = np.arange(nz)[:, None, None]
+    v0 = (np.where(z < nz // 2, 1500.0, 2300.0) * np.ones((nz, ny, nx))).astype(np.float32)
+    vt = (v0 * (1 + 0.05 * rng.uniform(-1, 1, v0.shape))).astype(np.float32)
+    rec = np.array([(i, ny // 2, 3) for i in range(0, nx, 3)] + [(nx - 1, ny - 1, nz - 1)], np.int32)
+    g = Geometry(nx=nx, ny=ny, nz=nz, h=10.0, dt=1e-3, nt=nt, nbl=nbl, vmax=2500.0)
+    return synth.Shot("small", g, 25.0, (nx // 3, ny // 2, 4), rec, vt, v0)
+
+
+@pytest.fixture(scope="module")
+def two_layer(oracle):
+    """The plain-gradient case (64^3, 200 steps of 1 ms).  Within 0.2 s no
+    wave scattered by the centre blob reaches the z=4 receivers, so data of the
+    specified true model differ from the two-layer data only below FP32
+    resolution; gradient parity therefore uses d_obs = 0 (Phi = 1/2 |d_sim|^2),
+    which drives the same sweeps with a residual of full size."""
+    from paper_2009_12623_gb300 import synth
+    shot = synth.two_layer_shot()
+    return shot, np.zeros((shot.geom.nt, len(shot.rec)))
+
+
+def phi_tol(d_sim, resid):
+    # Phi changes by <r, dd> for a data change dd; |dd| <= TOL |d_sim| in FP32
+    return 2 * TOL * np.linalg.norm(d_sim) * np.linalg.norm(resid) + 1e-30
+
+
+def _dev(cuda, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(cuda)
+
+
+@pytest.mark.parametrize("which", ["two_layer", "ragged"])
+def test_forward_records_match_oracle(cuda, oracle, two_layer, which):
+    from paper_2009_12623_gb300 import api, synth
+    shot = two_layer[0] if which == "two_layer" else _small_shot()
+    m = synth.slowness2(shot.v0)
+    ref, ub, ul = oracle.forward(_og(oracle, shot.geom), m.astype(np.float64), shot.wavelet.astype(np.float64),
+                                 shot.src, shot.rec, return_state=True)
+    d, up, ulast = api.forward(shot.geom, _dev(cuda, m), shot.wavelet, shot.src, _dev(cuda, shot.rec),
+                               return_state=True)
+    assert rel(d.cpu().numpy(), ref) < TOL
+    assert rel(ulast.cpu().numpy(), ul) < TOL
+    assert rel(up.cpu().numpy(), ub) < TOL
+
+
+def test_forward_from_state(cuda, oracle):
+    from paper_2009_12623_gb300 import api, synth
+    shot = _small_shot(nt=15)
+    rng = np.random.default_rng(3)
+    u0 = rng.normal(size=shot.geom.shape).astype(np.float32)
+    u1 = rng.normal(size=shot.geom.shape).astype(np.float32)
+    m = synth.slowness2(shot.v0)
+    ref, _, ul = oracle.forward(_og(oracle, shot.geom), m.astype(np.float64), shot.wavelet.astype(np.float64),
+                                shot.src, shot.rec, u_prev_init=u0.astype(np.float64),
+                                u_cur_init=u1.astype(np.float64), return_state=True)
+    d, _, ulast = api.forward(shot.geom, _dev(cuda, m), shot.wavelet, shot.src, _dev(cuda, shot.rec),
+                              u_prev_init=_dev(cuda, u0), u_cur_init=_dev(cuda, u1), return_state=True)
+    assert rel(ulast.cpu().numpy(), ul) < TOL
+    assert rel(d.cpu().numpy(), ref) < TOL
+
+
+def _grad(cuda, shot, d_obs, mode, k=1, atol=0.0, cap=1 << 30):
+    from paper_2009_12623_gb300 import api, synth
+    m = synth.slowness2(shot.v0)
+    with api.CheckpointStore(cap) as st:
+        g, phi = api.gradient(shot.geom, _dev(cuda, m), shot.wavelet, shot.src, _dev(cuda, shot.rec),
+                              _dev(cuda, np.asarray(d_obs, np.float32)), st, mode=mode, k=k, atol=atol)
+        stats = st.stats()
+    return g.cpu().numpy(), phi, stats
+
+
+def test_gradient_raw_matches_oracle(cuda, oracle, two_layer):
+    from paper_2009_12623_gb300 import synth
+    shot, d_obs = two_layer
+    og = _og(oracle, shot.geom)
+    gref, phiref, dsim, _ = oracle.gradient(og, synth.slowness2(shot.v0).astype(np.float64),
+                                            shot.wavelet.astype(np.float64), shot.src, shot.rec, d_obs)
+    g, phi, _ = _grad(cuda, shot, d_obs, 1)
+    assert rel(g, gref) < TOL
+    assert abs(phi - phiref) <= phi_tol(dsim, dsim - d_obs)
+
+
+def test_specified_true_model_residual_is_below_fp32_resolution(cuda, oracle):
+    """The true-model data of the plain-gradient case match the two-layer data
+    to within the FP32 tolerance, on both sides."""
+    from paper_2009_12623_gb300 import api, synth
+    shot = synth.two_layer_shot()
+    og = _og(oracle, shot.geom)
+    w = shot.wavelet.astype(np.float64)
+    d_true = oracle.forward(og, synth.slowness2(shot.v_true).astype(np.float64), w, shot.src, shot.rec)
+    d0 = oracle.forward(og, synth.slowness2(shot.v0).astype(np.float64), w, shot.src, shot.rec)
+    assert rel(d0, d_true) < 1e-5
+    d_gpu = api.forward(shot.geom, _dev(cuda, synth.slowness2(shot.v0)), shot.wavelet, shot.src,
+                        _dev(cuda, shot.rec)).cpu().numpy()
+    assert rel(d_gpu, d_true) < TOL
+
+
+def test_gradient_ragged_every_k(cuda, oracle):
+    from paper_2009_12623_gb300 import synth
+    shot = _small_shot()
+    og = _og(oracle, shot.geom)
+    d_obs = oracle.forward(og, synth.slowness2(shot.v_true).astype(np.float64), shot.wavelet.astype(np.float64),
+                           shot.src, shot.rec)
+    gref, phiref, dsim, _ = oracle.gradient(og, synth.slowness2(shot.v0).astype(np.float64),
+                                            shot.wavelet.astype(np.float64), shot.src, shot.rec, d_obs)
+    g, phi, _ = _grad(cuda, shot, d_obs, 2, k=7)
+    assert rel(g, gref) < TOL
+    assert abs(phi - phiref) <= phi_tol(dsim, dsim - d_obs)
+
+
+@pytest.mark.parametrize("k", [1, 4, 10, 33, 500])
+def test_every_k_raw_bitwise_equals_full_history(cuda, two_layer, k):
+    """Checkpointing alone is bitwise exact (Sec. 1.2) on the GPU too."""
+    shot, d_obs = two_layer
+    g_full, phi_full, _ = _grad(cuda, shot, d_obs, 1)
+    g_k, phi_k, _ = _grad(cuda, shot, d_obs, 2, k=k)
+    assert np.array_equal(g_full, g_k) and phi_full == phi_k
+
+
+def test_compressed_gradient_tracks_oracle(cuda, oracle, two_layer):
+    """Plain checkpointed gradient: every 10 steps, atol = 1e-4.  Both sides
+    compress their own (FP32 vs FP64-rounded) checkpoints, so the lossy
+    gradients differ by about the compression error itself; the GPU error
+    against the uncompressed FP64 gradient must match the oracle's."""
+    from paper_2009_12623_gb300 import synth
+    shot, d_obs = two_layer
+    og = _og(oracle, shot.geom)
+    m = synth.slowness2(shot.v0).astype(np.float64)
+    w = shot.wavelet.astype(np.float64)
+    g_raw, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs)
+    g_oz, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs, mode=2, k=10, atol=1e-4)
+    g_gz, _, stats = _grad(cuda, shot, d_obs, 2, k=10, atol=1e-4)
+    e_o, e_g = rel(g_oz, g_raw), rel(g_gz, g_raw)
+    assert e_g <= 1.5 * e_o + TOL, (e_g, e_o)
+    assert stats["used_bytes"] < stats["raw_bytes"]
+
+
+@pytest.mark.parametrize("atol", [1e-6, 1e-9])
+def test_compressed_full_history_converges(cuda, oracle, two_layer, atol):
+    from paper_2009_12623_gb300 import synth
+    shot, d_obs = two_layer
+    og = _og(oracle, shot.geom)
+    g_raw, *_ = oracle.gradient(og, synth.slowness2(shot.v0).astype(np.float64),
+                                shot.wavelet.astype(np.float64), shot.src, shot.rec, d_obs)
+    g, _, stats = _grad(cuda, shot, d_obs, 1, atol=atol)
+    assert rel(g, g_raw) < (1e-3 if atol > 1e-8 else TOL)
+    assert not stats["overflowed"]
+
+
+def test_capacity_overflow_reported(cuda, two_layer):
+    from paper_2009_12623_gb300 import api, synth, _lib
+    shot, d_obs = two_layer
+    m = synth.slowness2(shot.v0)
+    grad = torch.zeros(shot.geom.shape, device=cuda)
+    for atol in (0.0, 1e-4):
+        with api.CheckpointStore(1 << 20) as st:
+            with pytest.raises(api.FwiError) as e:
+                api.gradient(shot.geom, _dev(cuda, m), shot.wavelet, shot.src, _dev(cuda, shot.rec),
+                             _dev(cuda, d_obs.astype(np.float32)), st, mode=1, atol=atol, grad=grad)
+            assert e.value.status == _lib.FWI_ERR_CAPACITY
+            s = st.stats()
+            assert s["overflowed"] and s["used_bytes"] > (1 << 20)
+    assert float(grad.abs().max()) == 0.0
+
+
+def test_gradient_host_equals_device(cuda, two_layer):
+    from paper_2009_12623_gb300 import api, synth
+    shot, d_obs = two_layer
+    g_dev, phi_dev, _ = _grad(cuda, shot, d_obs, 2, k=10, atol=1e-4)
+    with api.CheckpointStore(1 << 30) as st:
+        g_host, phi_host = api.gradient_host(shot.geom, synth.slowness2(shot.v0), shot.wavelet, shot.src,
+                                             shot.rec, d_obs.astype(np.float32), st, mode=2, k=10, atol=1e-4)
+    assert np.array_equal(g_host, g_dev) and phi_host == phi_dev
+
+
+def test_misfit_and_dot_f64(cuda):
+    from paper_2009_12623_gb300 import api
+    rng = np.random.default_rng(0)
+    a = rng.normal(size=100003).astype(np.float32)
+    b = rng.normal(size=100003).astype(np.float32)
+    r, phi = api.misfit(_dev(cuda, a), _dev(cuda, b))
+    d = a.astype(np.float64) - b
+    assert np.array_equal(r.cpu().numpy(), a - b)
+    assert phi == pytest.approx(0.5 * np.sum((a - b).astype(np.float64) ** 2), rel=1e-12)
+    assert api.dot_f64(_dev(cuda, a), _dev(cuda, b)) == pytest.approx(np.dot(a.astype(np.float64), b), rel=1e-12)
+    del d
+
+
+def test_bad_receiver_rejected(cuda):
+    from paper_2009_12623_gb300 import api, synth
+    shot = _small_shot(nt=3)
+    rec = shot.rec.copy()
+    rec[0, 0] = shot.geom.nx + 5
+    with pytest.raises(api.FwiError):
+        api.forward(shot.geom, _dev(cuda, synth.slowness2(shot.v0)), shot.wavelet, shot.src, _dev(cuda, rec))
