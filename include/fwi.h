@@ -177,6 +177,28 @@ int zfp_compress_fixed_accuracy(const float* d_in, int nx, int ny, int nz, doubl
 int zfp_decompress(const void* d_in, size_t in_bytes, float* d_out, int nx, int ny, int nz,
                    void* stream);
 
+/* Allocation-free variant of zfp_compress_fixed_accuracy, same arguments,
+ * results and stream.  The paper has no counterpart: this exists for callers
+ * that cannot allocate device memory mid-run (a solver that has given nearly
+ * all free HBM to its checkpoint arena, or an application whose memory policy
+ * forbids allocations after start-up).  The regular call takes its encoder
+ * scratch from the stream-ordered pool; this one uses a fixed block of about
+ * 1 MiB inside the library's device image, held on every GPU that loads the
+ * library until exit, and calls no cudaMalloc, cudaMallocAsync, cudaFree or
+ * allocating library routine.
+ *   - Fields of more than 16,777,216 blocks of 4x4x4 (131,072 chunks) are
+ *     rejected with FWI_ERR_ARG before any device work.
+ *   - All calls share the block and it keeps the last call's contents; each
+ *     call clears what must start at zero.  Calls that overlap on the GPU
+ *     (other streams or host threads) race on it.
+ *   - The first call on a device looks up the block's address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ * Synchronises. */
+int zfp_compress_fixed_accuracy_noalloc(const float* d_in, int nx, int ny, int nz, double atol,
+                                        void* d_out, size_t out_capacity, size_t* h_out_bytes,
+                                        void* stream);
+
 /* ---- FP64 reductions ------------------------------------------------------ */
 /* d_resid = d_sim - d_obs (may alias d_sim); *h_misfit = 1/2 sum resid^2 in
  * FP64 (Eq. (3)).  Synchronises. */

@@ -23,7 +23,7 @@ EXPORTS = [
     "fwi_forward", "fwi_gradient", "fwi_gradient_host", "zfp_max_compressed_bytes",
     "zfp_compress_fixed_accuracy", "zfp_decompress", "fwi_misfit", "fwi_dot_f64",
     "fwi_status_string", "fwi_kernel_launch_count", "fwi_profile_enable", "fwi_profile_reset",
-    "fwi_profile_read",
+    "fwi_profile_read", "zfp_compress_fixed_accuracy_noalloc",
 ]
 KERNEL_CLASSES = ["stencil_forward", "stencil_adjoint_imaging", "zfp_encode", "zfp_decode", "other"]
 
@@ -81,6 +81,7 @@ def load() -> C.CDLL:
         L.zfp_max_compressed_bytes.restype = C.c_size_t
         L.zfp_compress_fixed_accuracy.argtypes = [fp, C.c_int, C.c_int, C.c_int, C.c_double, vp,
                                                   C.c_size_t, C.POINTER(C.c_size_t), vp]
+        L.zfp_compress_fixed_accuracy_noalloc.argtypes = L.zfp_compress_fixed_accuracy.argtypes
         L.zfp_decompress.argtypes = [vp, C.c_size_t, fp, C.c_int, C.c_int, C.c_int, vp]
         L.fwi_misfit.argtypes = [fp, fp, C.c_size_t, fp, dp, vp]
         L.fwi_dot_f64.argtypes = [fp, fp, C.c_size_t, dp, vp]
