@@ -145,9 +145,12 @@ def workload(args, rank):
     import numpy as np
     from paper_2009_12623_gb300 import synth
     nx, ny, nz = (int(v) for v in args.grid.split(","))
-    # one shot per rank: sources spread along x just under the water surface
-    sx = nx // 2 + (rank * 40) % max(1, nx // 2 - 40)
-    shot = synth.overthrust_like_shot(nx=nx, ny=ny, nz=nz, nt=args.nt, src_xy=(sx, ny // 2))
+    nbl = min(40, min(nx, ny, nz) // 6)
+    # one shot per rank: sources 40 cells apart along x (wrapping inside the
+    # absorbing layer), just under the water surface
+    lo, hi = nbl + 1, nx - nbl - 2
+    sx = lo + (nx // 2 - lo + 40 * rank) % max(1, hi - lo + 1)
+    shot = synth.overthrust_like_shot(nx=nx, ny=ny, nz=nz, nt=args.nt, nbl=nbl, src_xy=(sx, ny // 2))
     return shot, np.float32
 
 

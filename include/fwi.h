@@ -150,7 +150,7 @@ int fwi_gradient_host(const fwi_geometry* g, const float* h_m, const float* h_wa
 /* ---- fixed-accuracy codec (Sec. 1.3) -------------------------------------- */
 /* Stream format (shared bit-for-bit with the CPU oracle):
  *   64-byte header (magic "FCZ1", version, nx, ny, nz, minexp, nblocks,
- *   chunk size 128, nchunks, payload words, total bytes, format params),
+ *   chunk size 32, nchunks, payload words, total bytes, format params),
  *   nchunks u64 chunk word offsets, nblocks u16 block bit lengths (padded to
  *   8 bytes), then the payload of u64 words.  Each 4x4x4 block (x fastest,
  *   blocks ordered x, y, z; edge blocks replicate the last plane) carries:
@@ -186,7 +186,7 @@ int zfp_decompress(const void* d_in, size_t in_bytes, float* d_out, int nx, int 
  * 1 MiB inside the library's device image, held on every GPU that loads the
  * library until exit, and calls no cudaMalloc, cudaMallocAsync, cudaFree or
  * allocating library routine.
- *   - Fields of more than 16,777,216 blocks of 4x4x4 (131,072 chunks) are
+ *   - Fields of more than 4,194,304 blocks of 4x4x4 (131,072 chunks of 32) are
  *     rejected with FWI_ERR_ARG before any device work.
  *   - All calls share the block and it keeps the last call's contents; each
  *     call clears what must start at zero.  Calls that overlap on the GPU

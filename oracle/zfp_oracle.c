@@ -21,7 +21,7 @@
  *
  * Stream layout (little endian):
  *   [0,64)    header: magic, version, nx, ny, nz, minexp, nblocks,
- *             chunk size (128 blocks), nchunks, payload words, total bytes,
+ *             chunk size (32 blocks), nchunks, payload words, total bytes,
  *             format parameters
  *   then      nchunks x u64   word offset of each chunk in the payload
  *   then      nblocks x u16   bit length of each block (padded to 8 bytes)
@@ -36,7 +36,7 @@
 
 #define ZO_S 25
 #define ZO_G 11
-#define ZO_CHUNK 128
+#define ZO_CHUNK 32
 #define ZO_MAXBITS (9 + 32 * 64 + 64)
 #define ZO_MAGIC 0x315A4346u /* "FCZ1" */
 #define ZO_VERSION 1u

@@ -7,17 +7,19 @@
 // embedded bit planes (planes = emax - minexp + 11, raised to 32 when fewer
 // than 3 planes would be dropped).
 //
-// GPU organisation: one thread per block, one CTA (128 threads) per chunk of
-// 128 consecutive blocks.  The 64 coefficients of a block live in registers;
-// two 32x32 bit-matrix transposes turn them into 64-bit plane masks, from
-// which the exact bit count of every plane is computed with popc/clz.  A CTA
-// scan of the counts and a decoupled look-back across chunks (chunk order is
-// the CTA's ticket order, so every predecessor is already resident) give each
-// chunk its word offset in one pass; the chunk's bits are then assembled in
-// shared memory and written with coalesced 64-bit stores.  Decoding reverses
-// this with one CTA per chunk: the chunk's words are staged in shared memory,
-// block offsets come from a scan of the u16 length table, and each thread
-// rebuilds its plane masks (ctz finds every newly significant coefficient).
+// GPU organisation: one thread per block, one warp per chunk of 32
+// consecutive blocks (4 independent warps per CTA, never synchronised with
+// each other).  The 64 coefficients of a block live in registers; two 32x32
+// bit-matrix transposes turn them into 64-bit plane masks, from which the
+// exact bit count of every plane is computed with popc/clz.  A warp scan of
+// the counts and a warp-parallel decoupled look-back across chunks (chunk
+// order is the warp's ticket order, so every predecessor is already resident)
+// give each chunk its word offset in one pass; the chunk's bits are assembled
+// in the warp's shared-memory buffer while the predecessors finish, then
+// written with coalesced 64-bit stores.  Decoding reverses this with one warp
+// per chunk: the chunk's words are staged in shared memory, block offsets come
+// from a warp scan of the u16 length table, and each thread rebuilds its plane
+// masks (ctz finds every newly significant coefficient).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,19 +31,23 @@ namespace {
 
 using namespace zblock;
 
-constexpr int kWordsMax = (ZC_CHUNK * ZC_MAXBITS + 63) / 64;  // 4242 words
+constexpr int kWordsMax = (ZC_CHUNK * ZC_MAXBITS + 63) / 64;  // 1061 words
+constexpr int kWarps = 4;                                       // chunks per CTA
+#ifndef FWI_ENC_MIN_CTAS
+#define FWI_ENC_MIN_CTAS 4  // resident CTAs per SM the staged encoder is compiled for
+#endif
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr long kSpinLimit = 1L << 24;
 
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // Shared-memory bit writer (words assembled with atomicOr, so neighbouring
@@ -69,6 +75,7 @@ struct SWriter {
 
 struct EncArgs {
   const float* in;
+  bool vec_ok;  // rows 16-byte aligned (pitch % 4 == 0 and aligned base)
   int nx, ny, nz;
   long pitch;
   long nbx, nby, nblocks, nchunks;
@@ -88,16 +95,15 @@ __device__ __forceinline__ void put_u64(uint8_t* p, unsigned long long v) {
   *reinterpret_cast<unsigned long long*>(p) = v;
 }
 
-__global__ void __launch_bounds__(ZC_CHUNK) k_encode(EncArgs a) {
-  __shared__ unsigned long long sbuf[kWordsMax + 1];
-  __shared__ int s_chunk;
-  __shared__ unsigned s_warp[ZC_CHUNK / 32];
-  __shared__ unsigned long long s_prefix;
-  const int tid = threadIdx.x;
-  if (tid == 0) s_chunk = (int)atomicAdd(a.ticket, 1u);
-  __syncthreads();
-  const long chunk = s_chunk;
-  const long blk = chunk * ZC_CHUNK + tid;
+__global__ void __launch_bounds__(ZC_CHUNK * kWarps, 4) k_encode_chained(EncArgs a) {
+  __shared__ unsigned long long sbuf_all[kWarps][kWordsMax + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long* sbuf = sbuf_all[wid];
+  long chunk = 0;
+  if (lane == 0) chunk = (long)atomicAdd(a.ticket, 1u);
+  chunk = __shfl_sync(0xffffffffu, chunk, 0);
+  if (chunk >= a.nchunks) return;  // whole warp (grid is rounded up to whole CTAs)
+  const long blk = chunk * ZC_CHUNK + lane;
   const bool valid = blk < a.nblocks;
   const unsigned long long base = a.base ? *a.base : 0ull;
   const unsigned long long avail = a.limit > base ? a.limit - base : 0ull;
@@ -108,6 +114,9 @@ __global__ void __launch_bounds__(ZC_CHUNK) k_encode(EncArgs a) {
   int planes = 0, emax = 0, nbits = 0;
   if (valid) {
     const long bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
+    const long xb = 4 * bx;
+    // 16-byte row loads when the 4 x values are in range and aligned
+    const bool vec = a.vec_ok && xb + 3 < a.nx;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const long z = min(4 * bz + k, (long)a.nz - 1);
@@ -115,45 +124,49 @@ __global__ void __launch_bounds__(ZC_CHUNK) k_encode(EncArgs a) {
       for (int j = 0; j < 4; ++j) {
         const long y = min(4 * by + j, (long)a.ny - 1);
         const float* row = a.in + a.pitch * (y + (long)a.ny * z);
+        const int o = 4 * j + 16 * k;
+        if (vec) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + xb));
+          u[o] = v.x;
+          u[o + 1] = v.y;
+          u[o + 2] = v.z;
+          u[o + 3] = v.w;
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) u[i + 4 * j + 16 * k] = __float_as_uint(__ldg(row + min(4 * bx + i, (long)a.nx - 1)));
+          for (int i = 0; i < 4; ++i) u[o + i] = __float_as_uint(__ldg(row + min(xb + i, (long)a.nx - 1)));
+        }
       }
     }
     if (!quantise(u, a.minexp, emax, planes)) atomicOr(a.status, ST_NONFINITE);
     nbits = count_bits(u, planes);
   }
 
-  // ---- CTA exclusive scan of bit counts ------------------------------------
-  const int lane = tid & 31, warp = tid >> 5;
+  // ---- warp exclusive scan of bit counts -------------------------------------
   unsigned incl = (unsigned)nbits;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += v;
   }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  unsigned warp_off = 0, total = 0;
-#pragma unroll
-  for (int w = 0; w < ZC_CHUNK / 32; ++w) {
-    if (w < warp) warp_off += s_warp[w];
-    total += s_warp[w];
-  }
-  const unsigned my_off = warp_off + incl - (unsigned)nbits;
+  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+  const unsigned my_off = incl - (unsigned)nbits;
   const unsigned W = (total + 63u) / 64u;
 
-  // ---- decoupled look-back over chunks --------------------------------------
-  if (tid == 0) {
-    unsigned long long prefix = 0;
-    if (chunk == 0) {
-      st_release(&a.desc[0], kFlagPre | W);
-    } else {
-      st_release(&a.desc[chunk], kFlagAgg | W);
-      long p = chunk - 1;
-      while (p >= 0) {
-        unsigned long long d;
+  // ---- decoupled look-back over chunks (32 predecessors per step) ------------
+  // The chunk's word count is published first and its inclusive prefix as
+  // soon as it is known, so the prefix frontier keeps pace with the warps in
+  // flight.  A descriptor packs flag (aggregate / inclusive prefix) and value
+  // in one 64-bit word, so relaxed loads and stores suffice.
+  if (lane == 0) st_relaxed(&a.desc[chunk], (chunk == 0 ? kFlagPre : kFlagAgg) | W);
+  unsigned long long prefix = 0;
+  if (chunk > 0) {
+    long top = chunk - 1;
+    while (true) {
+      const long idx = top - lane;
+      unsigned long long d = kFlagPre;  // before chunk 0: an inclusive prefix of 0
+      if (idx >= 0) {
         long spins = 0;
-        while (((d = ld_acquire(&a.desc[p])) >> 62) == 0ull) {
+        while (((d = ld_relaxed(&a.desc[idx])) >> 62) == 0ull) {
           if (++spins > kSpinLimit) {
             atomicOr(a.status, ST_TIMEOUT);
             d = kFlagPre;
@@ -161,29 +174,32 @@ __global__ void __launch_bounds__(ZC_CHUNK) k_encode(EncArgs a) {
           }
           __nanosleep(32);
         }
-        prefix += d & kValMask;
-        if ((d >> 62) == 2ull) break;
-        --p;
       }
-      st_release(&a.desc[chunk], kFlagPre | (prefix + W));
+      const unsigned pre = __ballot_sync(0xffffffffu, (d >> 62) == 2ull);
+      const int stop = pre ? __ffs(pre) - 1 : 31;  // nearest inclusive prefix
+      unsigned long long v = lane <= stop ? (d & kValMask) : 0ull;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      prefix += v;
+      if (pre) break;
+      top -= 32;
     }
-    s_prefix = prefix;
+    if (lane == 0) st_relaxed(&a.desc[chunk], kFlagPre | (prefix + W));
   }
-  for (unsigned w = tid; w < W; w += ZC_CHUNK) sbuf[w] = 0ull;
-  __syncthreads();
-  const unsigned long long prefix = s_prefix;
 
-  // ---- emit the bits into shared memory -----------------------------------
+  // ---- assemble the chunk's bits in the warp's shared-memory buffer ----------
+  for (unsigned w = lane; w < W; w += 32) sbuf[w] = 0ull;
+  __syncwarp();
   if (valid) {
     SWriter wr{sbuf, 0ull, (int)(my_off & 63u), (int)(my_off >> 6)};
     emit(wr, u, emax, planes);
     wr.flush();
   }
-  __syncthreads();
+  __syncwarp();
 
   // ---- write payload, tables and (last chunk) the header -------------------
   const unsigned long long pay = a.payload + 8ull * prefix;
-  for (unsigned w = tid; w < W; w += ZC_CHUNK) {
+  for (unsigned w = lane; w < W; w += 32) {
     const unsigned long long off = pay + 8ull * w;
     if (off + 8 <= avail) put_u64(out + off, sbuf[w]);
   }
@@ -191,16 +207,16 @@ __global__ void __launch_bounds__(ZC_CHUNK) k_encode(EncArgs a) {
     const unsigned long long off = a.length_table + 2ull * blk;
     if (off + 2 <= avail) *reinterpret_cast<uint16_t*>(out + off) = (uint16_t)nbits;
   }
-  if (tid == 0) {
+  if (lane == 0) {
     const unsigned long long off = a.chunk_table + 8ull * chunk;
     if (off + 8 <= avail) put_u64(out + off, prefix);
   }
   if (chunk == a.nchunks - 1) {
     // zero padding of the length table after the last block
     const unsigned long long lt_end = a.length_table + 2ull * a.nblocks;
-    for (unsigned long long off = lt_end + 2ull * tid; off < a.payload; off += 2ull * ZC_CHUNK)
+    for (unsigned long long off = lt_end + 2ull * lane; off < a.payload; off += 64ull)
       if (off + 2 <= avail) *reinterpret_cast<uint16_t*>(out + off) = 0;
-    if (tid == 0) {
+    if (lane == 0) {
       const unsigned long long words = prefix + W;
       const unsigned long long bytes = a.payload + 8ull * words;
       if (64 <= avail) {
@@ -224,10 +240,204 @@ __global__ void __launch_bounds__(ZC_CHUNK) k_encode(EncArgs a) {
   }
 }
 
+// ---- staged encoder (no inter-chunk dependency) --------------------------------
+// Pass 1: every warp codes its chunk into its own fixed staging slot
+// (kWordsMax words) and records the word count; pass 2: one CTA per tile of
+// kTile chunks adds the counts of all earlier tiles and of its own earlier
+// chunks, then copies the words into place (2x the compressed bytes of extra
+// traffic, no waiting between chunks).
+constexpr int kTile = 1024;  // chunks per compaction CTA
+
+struct StageArgs {
+  unsigned long long* stage;     // nchunks x kWordsMax words
+  unsigned* words;               // per-chunk word count
+  unsigned long long* tile_sum;  // per-tile word totals (zeroed before pass 1)
+  unsigned long long* offset;    // per-chunk word offset in the payload
+};
+
+__device__ __forceinline__ void gather_block(const EncArgs& a, long blk, uint32_t* u) {
+  const long bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
+  const long xb = 4 * bx;
+  const bool vec = a.vec_ok && xb + 3 < a.nx;  // 16-byte row loads when aligned and in range
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const long z = min(4 * bz + k, (long)a.nz - 1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long y = min(4 * by + j, (long)a.ny - 1);
+      const float* row = a.in + a.pitch * (y + (long)a.ny * z);
+      const int o = 4 * j + 16 * k;
+      if (vec) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(row + xb));
+        u[o] = v.x;
+        u[o + 1] = v.y;
+        u[o + 2] = v.z;
+        u[o + 3] = v.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) u[o + i] = __float_as_uint(__ldg(row + min(xb + i, (long)a.nx - 1)));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_ENC_MIN_CTAS) k_encode_stage(EncArgs a, StageArgs st) {
+  __shared__ unsigned long long sbuf_all[kWarps][kWordsMax + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long* sbuf = sbuf_all[wid];
+  const long chunk = (long)blockIdx.x * kWarps + wid;
+  if (chunk >= a.nchunks) return;  // whole warp
+  const long blk = chunk * ZC_CHUNK + lane;
+  const bool valid = blk < a.nblocks;
+  uint32_t u[64];
+  int planes = 0, emax = 0, nbits = 0;
+  if (valid) {
+    gather_block(a, blk, u);
+    if (!quantise(u, a.minexp, emax, planes)) atomicOr(a.status, ST_NONFINITE);
+    nbits = count_bits(u, planes);
+  }
+  unsigned incl = (unsigned)nbits;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+  const unsigned my_off = incl - (unsigned)nbits;
+  const unsigned W = (total + 63u) / 64u;
+  for (unsigned w = lane; w < W; w += 32) sbuf[w] = 0ull;
+  __syncwarp();
+  if (valid) {
+    SWriter wr{sbuf, 0ull, (int)(my_off & 63u), (int)(my_off >> 6)};
+    emit(wr, u, emax, planes);
+    wr.flush();
+  }
+  __syncwarp();
+  unsigned long long* dst = st.stage + chunk * (long)kWordsMax;
+  for (unsigned w = lane; w < W; w += 32) dst[w] = sbuf[w];
+  if (valid) {
+    const unsigned long long base = a.base ? *a.base : 0ull;
+    const unsigned long long avail = a.limit > base ? a.limit - base : 0ull;
+    const unsigned long long off = a.length_table + 2ull * blk;
+    if (off + 2 <= avail) *reinterpret_cast<uint16_t*>(a.out + base + off) = (uint16_t)nbits;
+  }
+  if (lane == 0) {
+    st.words[chunk] = W;
+    atomicAdd(&st.tile_sum[chunk / kTile], (unsigned long long)W);
+  }
+}
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;
+}
+
+// Chunk offsets: one CTA (256 threads, 4 chunks per thread) per tile of kTile
+// chunks adds the totals of the earlier tiles to a scan of its own chunks.
+__global__ void __launch_bounds__(256) k_encode_compact(EncArgs a, StageArgs st) {
+  __shared__ unsigned long long red[8];
+  __shared__ unsigned long long wsum[8];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const long tile = blockIdx.x;
+  const long c0 = tile * kTile;
+  const unsigned long long base = a.base ? *a.base : 0ull;
+  const unsigned long long avail = a.limit > base ? a.limit - base : 0ull;
+  uint8_t* out = a.out + base;
+  // words of all earlier tiles
+  unsigned long long pre = 0;
+  for (long t = tid; t < tile; t += blockDim.x) pre += st.tile_sum[t];
+  pre = block_sum_u64(pre, red);
+  // exclusive scan of this tile's chunk word counts (4 consecutive per thread)
+  unsigned cw[4];
+  unsigned mine = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long c = c0 + 4 * tid + i;
+    cw[i] = c < a.nchunks ? st.words[c] : 0u;
+    mine += cw[i];
+  }
+  unsigned long long incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  unsigned long long woff = 0, tile_total = 0;
+  for (int i = 0; i < 8; ++i) {
+    if (i < w) woff += wsum[i];
+    tile_total += wsum[i];
+  }
+  unsigned long long off = pre + woff + incl - mine;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long c = c0 + 4 * tid + i;
+    if (c < a.nchunks) {
+      st.offset[c] = off;
+      const unsigned long long t = a.chunk_table + 8ull * c;
+      if (t + 8 <= avail) put_u64(out + t, off);
+    }
+    off += cw[i];
+  }
+  if (tile == (a.nchunks - 1) / kTile) {
+    // zero padding of the length table after the last block, header, size
+    const unsigned long long lt_end = a.length_table + 2ull * a.nblocks;
+    for (unsigned long long o = lt_end + 2ull * tid; o < a.payload; o += 2ull * blockDim.x)
+      if (o + 2 <= avail) *reinterpret_cast<uint16_t*>(out + o) = 0;
+    if (tid == 0) {
+      const unsigned long long words = pre + tile_total;
+      const unsigned long long bytes = a.payload + 8ull * words;
+      if (64 <= avail) {
+        put_u32(out + 0, ZC_MAGIC);
+        put_u32(out + 4, ZC_VERSION);
+        put_u32(out + 8, (uint32_t)a.nx);
+        put_u32(out + 12, (uint32_t)a.ny);
+        put_u32(out + 16, (uint32_t)a.nz);
+        put_u32(out + 20, (uint32_t)a.minexp);
+        put_u64(out + 24, (unsigned long long)a.nblocks);
+        put_u32(out + 32, (uint32_t)ZC_CHUNK);
+        put_u32(out + 36, (uint32_t)a.nchunks);
+        put_u64(out + 40, words);
+        put_u64(out + 48, bytes);
+        put_u32(out + 56, (uint32_t)(ZC_S | (ZC_G << 8)));
+        put_u32(out + 60, 0u);
+      }
+      if (bytes > avail) atomicOr(a.status, ST_CAPACITY);
+      *a.size_out = bytes;
+    }
+  }
+}
+
+// Placement: one warp per chunk moves its staged words to their offset.
+__global__ void __launch_bounds__(256) k_encode_place(EncArgs a, StageArgs st) {
+  const int lane = threadIdx.x & 31;
+  const long chunk = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (chunk >= a.nchunks) return;
+  const unsigned long long base = a.base ? *a.base : 0ull;
+  const unsigned long long avail = a.limit > base ? a.limit - base : 0ull;
+  uint8_t* out = a.out + base;
+  const unsigned n = st.words[chunk];
+  const unsigned long long pay = a.payload + 8ull * st.offset[chunk];
+  const unsigned long long* from = st.stage + chunk * (long)kWordsMax;
+  for (unsigned k = lane; k < n; k += 32) {
+    const unsigned long long dst = pay + 8ull * k;
+    if (dst + 8 <= avail) put_u64(out + dst, from[k]);
+  }
+}
+
 // ---- decoder ------------------------------------------------------------------
 
 struct DecArgs {
   const uint8_t* in;
+  bool vec_ok;
   const unsigned long long* base;
   unsigned long long avail;  // bytes readable from the stream start (when base == NULL)
   unsigned long long limit;  // bytes readable from `in` (when base != NULL)
@@ -239,6 +449,8 @@ struct DecArgs {
   int* status;
 };
 
+// Bit reader over a chunk staged in shared memory (two zero words follow the
+// chunk, so a peek at the end stays inside the buffer).
 struct SReader {
   const unsigned long long* buf;
   long pos;
@@ -257,20 +469,19 @@ __device__ __forceinline__ unsigned long long get_u64(const uint8_t* p) {
   return *reinterpret_cast<const unsigned long long*>(p);
 }
 
-__global__ void __launch_bounds__(ZC_CHUNK) k_decode(DecArgs a) {
-  __shared__ unsigned long long sbuf[kWordsMax + 2];
-  __shared__ unsigned s_warp[ZC_CHUNK / 32];
-  __shared__ unsigned long long s_first, s_words;
-  __shared__ int s_minexp, s_bad;
-  const int tid = threadIdx.x;
-  const long chunk = blockIdx.x;
+__global__ void __launch_bounds__(ZC_CHUNK * kWarps, 4) k_decode(DecArgs a) {
+  __shared__ unsigned long long sbuf_all[kWarps][kWordsMax + 2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long* sbuf = sbuf_all[wid];
+  const long chunk = (long)blockIdx.x * kWarps + wid;
+  if (chunk >= a.nchunks) return;  // whole warp
   const unsigned long long base = a.base ? *a.base : 0ull;
   const unsigned long long avail = a.base ? (a.limit > base ? a.limit - base : 0ull) : a.avail;
   const uint8_t* in = a.in + base;
-  if (tid == 0) {
-    int bad = 0;
-    unsigned long long first = 0, words = 0;
-    int minexp = 0;
+  int bad = 0;
+  unsigned long long first = 0, words = 0;
+  int minexp = 0;
+  if (lane == 0) {
     if (a.payload > avail || get_u32(in) != ZC_MAGIC || get_u32(in + 4) != ZC_VERSION ||
         (int)get_u32(in + 8) != a.nx || (int)get_u32(in + 12) != a.ny ||
         (int)get_u32(in + 16) != a.nz || get_u64(in + 24) != (unsigned long long)a.nblocks ||
@@ -288,55 +499,48 @@ __global__ void __launch_bounds__(ZC_CHUNK) k_decode(DecArgs a) {
         bad = 1;
       words = next - first;
     }
-    s_first = first;
-    s_words = words;
-    s_minexp = minexp;
-    s_bad = bad;
   }
-  __syncthreads();
-  if (s_bad) {
-    if (tid == 0) atomicOr(a.status, ST_CORRUPT);
+  bad = __shfl_sync(0xffffffffu, bad, 0);
+  if (bad) {
+    if (lane == 0) atomicOr(a.status, ST_CORRUPT);
     return;
   }
-  const long blk = chunk * ZC_CHUNK + tid;
+  first = __shfl_sync(0xffffffffu, first, 0);
+  words = __shfl_sync(0xffffffffu, words, 0);
+  minexp = __shfl_sync(0xffffffffu, minexp, 0);
+  const long blk = chunk * ZC_CHUNK + lane;
   const bool valid = blk < a.nblocks;
   const int len = valid ? (int)*reinterpret_cast<const uint16_t*>(in + a.length_table + 2ull * blk) : 0;
-  // CTA exclusive scan of block lengths
-  const int lane = tid & 31, warp = tid >> 5;
+  // stage the chunk's words and scan the block lengths
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in + a.payload) + first;
+  for (unsigned long long w = lane; w < words; w += 32) sbuf[w] = __ldg(src + w);
+  if (lane < 2) sbuf[words + lane] = 0ull;
   unsigned incl = (unsigned)len;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += v;
   }
-  if (lane == 31) s_warp[warp] = incl;
-  const unsigned long long W = s_words;
-  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in + a.payload) + s_first;
-  for (unsigned long long w = tid; w < W; w += ZC_CHUNK) sbuf[w] = __ldg(src + w);
-  if (tid < 2) sbuf[W + tid] = 0ull;
-  __syncthreads();
-  unsigned warp_off = 0, total = 0;
-#pragma unroll
-  for (int w = 0; w < ZC_CHUNK / 32; ++w) {
-    if (w < warp) warp_off += s_warp[w];
-    total += s_warp[w];
-  }
-  if ((unsigned long long)total > 64ull * W) {
-    if (tid == 0) atomicOr(a.status, ST_CORRUPT);
+  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  if ((unsigned long long)total > 64ull * words) {
+    if (lane == 0) atomicOr(a.status, ST_CORRUPT);
     return;
   }
   if (!valid) return;
-  const long start = (long)(warp_off + incl - (unsigned)len);
+  const long start = (long)(incl - (unsigned)len);
   SReader rd{sbuf, start, start + len};
   uint32_t u[64];
   int emax = 0, planes = 0;
-  if (!decode_planes(rd, s_minexp, u, emax, planes) || rd.pos != rd.end) {
+  if (!decode_planes(rd, minexp, u, emax, planes) || rd.pos != rd.end) {
     atomicOr(a.status, ST_CORRUPT);
     return;
   }
   float v[64];
   dequantise(u, emax, planes, v);
   const long bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
+  const long xb = 4 * bx;
+  const bool vec = a.vec_ok && xb + 3 < a.nx;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const long z = 4 * bz + k;
@@ -345,10 +549,13 @@ __global__ void __launch_bounds__(ZC_CHUNK) k_decode(DecArgs a) {
       const long y = 4 * by + j;
       if (z < a.nz && y < a.ny) {
         float* row = a.out + a.pitch * (y + (long)a.ny * z);
+        const int o = 4 * j + 16 * k;
+        if (vec) {
+          *reinterpret_cast<float4*>(row + xb) = make_float4(v[o], v[o + 1], v[o + 2], v[o + 3]);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const long x = 4 * bx + i;
-          if (x < a.nx) row[x] = v[i + 4 * j + 16 * k];
+          for (int i = 0; i < 4; ++i)
+            if (xb + i < a.nx) row[xb + i] = v[o + i];
         }
       }
     }
@@ -377,17 +584,14 @@ ZLayout zlayout(int nx, int ny, int nz) {
   return L;
 }
 
-size_t zfp_encode_scratch_words(int nx, int ny, int nz) {
-  return (size_t)zlayout(nx, ny, nz).nchunks + 1;
-}
 
-static cudaError_t encode_common(const float* in, Grid g, int minexp, uint8_t* out,
-                                 const unsigned long long* d_base, size_t capacity,
-                                 unsigned long long* d_size, int* d_status,
-                                 unsigned long long* scratch, cudaStream_t s) {
+static EncArgs encode_args(const float* in, Grid g, int minexp, uint8_t* out,
+                           const unsigned long long* d_base, size_t capacity,
+                           unsigned long long* d_size, int* d_status) {
   ZLayout L = zlayout(g.nx, g.ny, g.nz);
   EncArgs a;
   a.in = in;
+  a.vec_ok = (g.pitch % 4 == 0) && (((uintptr_t)in & 15) == 0);
   a.nx = g.nx;
   a.ny = g.ny;
   a.nz = g.nz;
@@ -405,23 +609,59 @@ static cudaError_t encode_common(const float* in, Grid g, int minexp, uint8_t* o
   a.payload = L.payload;
   a.size_out = d_size;
   a.status = d_status;
-  a.desc = scratch;
-  a.ticket = reinterpret_cast<unsigned int*>(scratch + L.nchunks);
-  const int ps = prof_begin(KC_ZFP_ENCODE, s);
-  k_encode<<<(unsigned)L.nchunks, ZC_CHUNK, 0, s>>>(a);
-  prof_end(ps, s);
-  count_launch();
-  return cudaGetLastError();
+  a.desc = nullptr;
+  a.ticket = nullptr;
+  return a;
+}
+
+size_t zfp_encode_scratch_bytes(int nx, int ny, int nz) {
+  ZLayout L = zlayout(nx, ny, nz);
+  const size_t ntiles = (size_t)((L.nchunks + kTile - 1) / kTile);
+  return (size_t)L.nchunks * kWordsMax * 8 + (size_t)L.nchunks * 12 + ntiles * 8 + 256;
 }
 
 cudaError_t zfp_encode_launch(const float* in, Grid g, int minexp, uint8_t* out,
                               const unsigned long long* d_base, size_t capacity,
-                              unsigned long long* d_size, int* d_status,
-                              unsigned long long* scratch, cudaStream_t s) {
-  size_t words = zfp_encode_scratch_words(g.nx, g.ny, g.nz);
-  cudaError_t e = cudaMemsetAsync(scratch, 0, words * 8, s);
+                              unsigned long long* d_size, int* d_status, void* scratch,
+                              cudaStream_t s) {
+  EncArgs a = encode_args(in, g, minexp, out, d_base, capacity, d_size, d_status);
+  const long ntiles = (a.nchunks + kTile - 1) / kTile;
+  StageArgs st;
+  st.stage = static_cast<unsigned long long*>(scratch);
+  st.tile_sum = st.stage + (size_t)a.nchunks * kWordsMax;
+  st.offset = st.tile_sum + ntiles;
+  st.words = reinterpret_cast<unsigned*>(st.offset + a.nchunks);
+  cudaError_t e = cudaMemsetAsync(st.tile_sum, 0, ntiles * 8, s);
   if (e != cudaSuccess) return e;
-  return encode_common(in, g, minexp, out, d_base, capacity, d_size, d_status, scratch, s);
+  const int ps = prof_begin(KC_ZFP_ENCODE, s);
+  k_encode_stage<<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, 0, s>>>(a, st);
+  k_encode_compact<<<(unsigned)ntiles, 256, 0, s>>>(a, st);
+  k_encode_place<<<(unsigned)((a.nchunks + 7) / 8), 256, 0, s>>>(a, st);
+  prof_end(ps, s);
+  count_launch();
+  count_launch();
+  count_launch();
+  return cudaGetLastError();
+}
+
+size_t zfp_encode_chained_scratch_words(int nx, int ny, int nz) {
+  return (size_t)zlayout(nx, ny, nz).nchunks + 1;
+}
+
+cudaError_t zfp_encode_chained_launch(const float* in, Grid g, int minexp, uint8_t* out,
+                                      const unsigned long long* d_base, size_t capacity,
+                                      unsigned long long* d_size, int* d_status,
+                                      unsigned long long* scratch, cudaStream_t s) {
+  EncArgs a = encode_args(in, g, minexp, out, d_base, capacity, d_size, d_status);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)(a.nchunks + 1) * 8, s);
+  if (e != cudaSuccess) return e;
+  a.desc = scratch;
+  a.ticket = reinterpret_cast<unsigned int*>(scratch + a.nchunks);
+  const int ps = prof_begin(KC_ZFP_ENCODE, s);
+  k_encode_chained<<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, 0, s>>>(a);
+  prof_end(ps, s);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_base, size_t avail,
@@ -429,6 +669,7 @@ cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_bas
   ZLayout L = zlayout(g.nx, g.ny, g.nz);
   DecArgs a;
   a.in = in;
+  a.vec_ok = (g.pitch % 4 == 0) && (((uintptr_t)out & 15) == 0);
   a.base = d_base;
   a.avail = avail;
   a.limit = avail;
@@ -446,7 +687,7 @@ cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_bas
   a.payload = L.payload;
   a.status = d_status;
   const int ps = prof_begin(KC_ZFP_DECODE, s);
-  k_decode<<<(unsigned)L.nchunks, ZC_CHUNK, 0, s>>>(a);
+  k_decode<<<(unsigned)((L.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, 0, s>>>(a);
   prof_end(ps, s);
   count_launch();
   return cudaGetLastError();

@@ -103,25 +103,43 @@ FZ_HD void lift_inv(int& x0, int& x1, int& x2, int& x3) {
   x2 = a2;
   x3 = a3;
 }
-FZ_HD void xform_fwd(int* q) {
-#pragma unroll
-  for (int l = 0; l < 16; ++l) lift_fwd(q[4 * l], q[4 * l + 1], q[4 * l + 2], q[4 * l + 3]);
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) lift_fwd(q[i + 16 * k], q[i + 16 * k + 4], q[i + 16 * k + 8], q[i + 16 * k + 12]);
-#pragma unroll
-  for (int l = 0; l < 16; ++l) lift_fwd(q[l], q[l + 16], q[l + 32], q[l + 48]);
+// The block lives in 64 uint32 registers throughout; the transform reads and
+// writes them as two's-complement int32 (same bits, no extra registers).
+FZ_HD void lift_fwd_u(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t& a3) {
+  int x0 = (int)a0, x1 = (int)a1, x2 = (int)a2, x3 = (int)a3;
+  lift_fwd(x0, x1, x2, x3);
+  a0 = (uint32_t)x0;
+  a1 = (uint32_t)x1;
+  a2 = (uint32_t)x2;
+  a3 = (uint32_t)x3;
 }
-FZ_HD void xform_inv(int* q) {
+FZ_HD void lift_inv_u(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t& a3) {
+  int x0 = (int)a0, x1 = (int)a1, x2 = (int)a2, x3 = (int)a3;
+  lift_inv(x0, x1, x2, x3);
+  a0 = (uint32_t)x0;
+  a1 = (uint32_t)x1;
+  a2 = (uint32_t)x2;
+  a3 = (uint32_t)x3;
+}
+FZ_HD void xform_fwd(uint32_t* q) {
 #pragma unroll
-  for (int l = 0; l < 16; ++l) lift_inv(q[l], q[l + 16], q[l + 32], q[l + 48]);
+  for (int l = 0; l < 16; ++l) lift_fwd_u(q[4 * l], q[4 * l + 1], q[4 * l + 2], q[4 * l + 3]);
 #pragma unroll
   for (int k = 0; k < 4; ++k)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) lift_inv(q[i + 16 * k], q[i + 16 * k + 4], q[i + 16 * k + 8], q[i + 16 * k + 12]);
+    for (int i = 0; i < 4; ++i) lift_fwd_u(q[i + 16 * k], q[i + 16 * k + 4], q[i + 16 * k + 8], q[i + 16 * k + 12]);
 #pragma unroll
-  for (int l = 0; l < 16; ++l) lift_inv(q[4 * l], q[4 * l + 1], q[4 * l + 2], q[4 * l + 3]);
+  for (int l = 0; l < 16; ++l) lift_fwd_u(q[l], q[l + 16], q[l + 32], q[l + 48]);
+}
+FZ_HD void xform_inv(uint32_t* q) {
+#pragma unroll
+  for (int l = 0; l < 16; ++l) lift_inv_u(q[l], q[l + 16], q[l + 32], q[l + 48]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) lift_inv_u(q[i + 16 * k], q[i + 16 * k + 4], q[i + 16 * k + 8], q[i + 16 * k + 12]);
+#pragma unroll
+  for (int l = 0; l < 16; ++l) lift_inv_u(q[4 * l], q[4 * l + 1], q[4 * l + 2], q[4 * l + 3]);
 }
 
 // 32x32 bit-matrix transpose in registers: afterwards bit i of a[b] is what
@@ -170,21 +188,28 @@ FZ_HD bool quantise(uint32_t* u, int minexp, int& emax, int& planes) {
     emax = e > -127 ? e : -127;
     planes = planes_for(emax, minexp);
   }
-  // q = trunc(x 2^(S - emax)) from the integer significand, exactly
-  int q[64];
+  if (!planes) {  // nothing to code: skip the transform
+#pragma unroll
+    for (int i = 0; i < 64; ++i) u[i] = 0u;
+    return finite;
+  }
+  // q = trunc(x 2^(S - emax)) from the integer significand, exactly (in place)
 #pragma unroll
   for (int i = 0; i < 64; ++i) {
     const uint32_t bits = u[i];
     const int Eb = (int)((bits >> 23) & 0xffu);
     const uint32_t M = Eb ? ((bits & 0x7fffffu) | 0x800000u) : (bits & 0x7fffffu);
     const int sh = (Eb ? Eb : 1) - (150 - kS) - emax;
-    uint32_t mag = sh >= 0 ? (M << sh) : (sh > -32 ? (M >> (-sh)) : 0u);
-    if (!maxbits) mag = 0;
-    q[i] = (bits >> 31) ? -(int)mag : (int)mag;
+    const uint32_t mag = sh >= 0 ? (M << sh) : (sh > -32 ? (M >> (-sh)) : 0u);
+    u[i] = (bits >> 31) ? (0u - mag) : mag;
   }
-  xform_fwd(q);
+  xform_fwd(u);
+  // sequency order and negabinary, through a register permutation
+  uint32_t c[64];
 #pragma unroll
-  for (int p = 0; p < 64; ++p) u[p] = ((uint32_t)q[perm_at(p)] + kNB) ^ kNB;
+  for (int p = 0; p < 64; ++p) c[p] = (u[perm_at(p)] + kNB) ^ kNB;
+#pragma unroll
+  for (int p = 0; p < 64; ++p) u[p] = c[p];
   transpose32(u);
   transpose32(u + 32);
   return finite;
@@ -230,8 +255,12 @@ FZ_HD void emit(W& w, const uint32_t* u, int emax, int planes) {
           break;
         }
         const int j = ctz64(r);
-        w.put(1ull, 1);
-        w.put(1ull << j, j + 1);
+        if (j < 63) {
+          w.put(1ull | (1ull << (j + 1)), j + 2);  // group bit, then the run up to the 1
+        } else {
+          w.put(1ull, 1);
+          w.put(1ull << j, j + 1);
+        }
         n += j + 1;
         r = (j + 1 < 64) ? (r >> (j + 1)) : 0ull;
       }
@@ -307,10 +336,11 @@ FZ_HD void dequantise(uint32_t* u, int emax, int planes, float* v) {
   }
   transpose32(u);
   transpose32(u + 32);
-  int q[64];
+  uint32_t c[64];
 #pragma unroll
-  for (int p = 0; p < 64; ++p) q[perm_at(p)] = (int)((u[p] ^ kNB) - kNB);
-  xform_inv(q);
+  for (int p = 0; p < 64; ++p) c[perm_at(p)] = (u[p] ^ kNB) - kNB;
+  xform_inv(c);
+  const int* q = reinterpret_cast<const int*>(c);
   const int k = emax - kS;
   if (k >= -126) {
     const float scale = as_float((uint32_t)(k + 127) << 23);

@@ -1,19 +1,20 @@
 // Allocation-free variant of zfp_compress_fixed_accuracy.
 //
-// Why it exists: the regular entry point takes its scratch (the per-chunk
-// look-back descriptors of the one-pass encoder, the chunk ticket, the size
-// and status words) from the device's stream-ordered memory pool on every
-// call.  Some callers cannot allocate device memory mid-run -- for example a
+// Why it exists: the regular entry point takes its scratch (a staging slot
+// per chunk, about the size of the field, plus size and status words) from
+// the device's stream-ordered memory pool on every call.  Some callers cannot allocate device memory mid-run -- for example a
 // solver that has already handed nearly all free HBM to its checkpoint arena,
 // or an application whose memory policy forbids allocations after start-up.
-// This variant uses a fixed scratch block that lives in the library's own
-// device image instead, so it calls no cudaMalloc, cudaMallocAsync, cudaFree
-// or allocating library routine.
+// This variant runs the single-pass encoder (chunks find their offsets by a
+// decoupled look-back, so its scratch is one descriptor per chunk) with that
+// scratch in a fixed block inside the library's own device image, so it
+// calls no cudaMalloc, cudaMallocAsync, cudaFree or allocating library
+// routine.
 //
 // Limits and behaviour:
 //   - The scratch holds kMaxChunks descriptors: fields of up to
-//     kMaxChunks * 128 blocks of 4x4x4 values (16,777,216 blocks, about
-//     1.07e9 values).  Larger fields are rejected with FWI_ERR_ARG before any
+//     kMaxChunks * 32 blocks of 4x4x4 values (4,194,304 blocks, about
+//     2.7e8 values, e.g. 881 x 881 x 287).  Larger fields are rejected with FWI_ERR_ARG before any
 //     device work.
 //   - The block occupies about 1 MiB on every GPU that loads the library,
 //     until the process exits.
@@ -84,8 +85,8 @@ extern "C" int zfp_compress_fixed_accuracy_noalloc(const float* d_in, int nx, in
   const int minexp = e_frexp - 1;
   // the encoder clears its descriptors and ticket itself; clear the status here
   if (cudaMemsetAsync(d_status, 0, sizeof(int), s) != cudaSuccess ||
-      zfp_encode_launch(d_in, Grid{nx, ny, nz, nx}, minexp, (uint8_t*)d_out, nullptr, out_capacity,
-                        d_size, d_status, scratch, s) != cudaSuccess) {
+      zfp_encode_chained_launch(d_in, Grid{nx, ny, nz, nx}, minexp, (uint8_t*)d_out, nullptr,
+                                out_capacity, d_size, d_status, scratch, s) != cudaSuccess) {
     cudaGetLastError();
     return FWI_ERR_CUDA;
   }

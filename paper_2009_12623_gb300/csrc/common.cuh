@@ -49,7 +49,7 @@ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 // ---- codec layout -----------------------------------------------------------
 constexpr int ZC_S = 25;        // block-floating-point fraction bits
 constexpr int ZC_G = 11;        // guard planes
-constexpr int ZC_CHUNK = 128;   // blocks per chunk (one CTA)
+constexpr int ZC_CHUNK = 32;    // blocks per chunk (one warp)
 constexpr int ZC_MAXBITS = 9 + 32 * 64 + 64;
 constexpr uint32_t ZC_MAGIC = 0x315A4346u;  // "FCZ1"
 constexpr uint32_t ZC_VERSION = 1u;
@@ -62,15 +62,24 @@ struct ZLayout {
 ZLayout zlayout(int nx, int ny, int nz);
 
 // Compress one pitched field into out (device), which has `capacity` bytes
-// counted from the device offset *d_base (bytes; NULL = 0).  The stream size is
-// written to *d_size (device).  Sets flags in *d_status.  `scratch` holds
-// nchunks+1 u64 (zeroed here).  Asynchronous.
+// counted from the device offset *d_base (bytes; NULL = 0).  The stream size
+// is written to *d_size (device); flags go to *d_status.  Two passes with no
+// dependency between chunks: code every chunk into a fixed staging slot, then
+// one CTA per tile of chunks places the words.  `scratch` must hold
+// zfp_encode_scratch_bytes() bytes.  Asynchronous.
+size_t zfp_encode_scratch_bytes(int nx, int ny, int nz);
 cudaError_t zfp_encode_launch(const float* in, Grid g, int minexp, uint8_t* out,
                               const unsigned long long* d_base, size_t capacity,
-                              unsigned long long* d_size, int* d_status,
-                              unsigned long long* scratch, cudaStream_t s);
-// Scratch u64 words the encoder needs for an nx*ny*nz field.
-size_t zfp_encode_scratch_words(int nx, int ny, int nz);
+                              unsigned long long* d_size, int* d_status, void* scratch,
+                              cudaStream_t s);
+// Single-pass variant whose scratch is only nchunks+1 words (per-chunk
+// look-back descriptors and a ticket), zeroed here: chunks find their offset
+// by a decoupled look-back over their predecessors.  Same stream.
+size_t zfp_encode_chained_scratch_words(int nx, int ny, int nz);
+cudaError_t zfp_encode_chained_launch(const float* in, Grid g, int minexp, uint8_t* out,
+                                      const unsigned long long* d_base, size_t capacity,
+                                      unsigned long long* d_size, int* d_status,
+                                      unsigned long long* scratch, cudaStream_t s);
 
 // Decompress a stream located at in + *d_base (d_base NULL = 0) of at most
 // `avail` bytes into a pitched field.  Asynchronous; errors go to *d_status.

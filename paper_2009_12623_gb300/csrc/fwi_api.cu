@@ -419,7 +419,7 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
   double* d_part = pool.get<double>(reduce_scratch_doubles());
   unsigned long long* offs = pool.get<unsigned long long>(nslots + 1);
   unsigned long long* sizes = pool.get<unsigned long long>(nslots + 1);
-  unsigned long long* scratch = pool.get<unsigned long long>(zfp_encode_scratch_words(G.nx, G.ny, G.nz));
+  void* scratch = lossy ? (void*)pool.get<unsigned char>(zfp_encode_scratch_bytes(G.nx, G.ny, G.nz)) : nullptr;
   const int K = pol->mode == FWI_CKPT_EVERY_K ? pol->k_or_snaps : 1;
   std::vector<float*> ring(K, nullptr);
   for (int i = 0; i < K; ++i) ring[i] = pool.get<float>(G.cells());
@@ -583,11 +583,10 @@ int zfp_compress_fixed_accuracy(const float* d_in, int nx, int ny, int nz, doubl
     return FWI_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   Pool pool(s);
-  const size_t words = zfp_encode_scratch_words(nx, ny, nz);
-  unsigned long long* scratch = pool.get<unsigned long long>(words + 1);
+  void* scratch = pool.get<unsigned char>(zfp_encode_scratch_bytes(nx, ny, nz));
+  unsigned long long* d_size = pool.get<unsigned long long>(1);
   int* d_status = pool.get<int>(1);
   if (pool.failed) return FWI_ERR_NOMEM;
-  unsigned long long* d_size = scratch + words;
   CK(cudaMemsetAsync(d_status, 0, sizeof(int), s));
   CK(zfp_encode_launch(d_in, Grid{nx, ny, nz, nx}, minexp_of(atol), (uint8_t*)d_out, nullptr,
                        out_capacity, d_size, d_status, scratch, s));
