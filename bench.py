@@ -183,9 +183,10 @@ def source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, launch_scale: float):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current source of that kernel (else None)."""
+def measured_traffic(kernel: str, cells: int):
+    """DRAM bytes per launch from the committed ncu summary (scaled from the
+    captured case by cells), if it was taken on the current source of that
+    kernel (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(path))
@@ -194,7 +195,7 @@ def measured_traffic(kernel: str, launch_scale: float):
     e = d.get(kernel)
     if not e or e.get("source_hash") != source_hash(kernel):
         return None
-    return e["dram_bytes_per_launch"] * launch_scale / e.get("cells", 1) if "cells" in e else None
+    return round(e["dram_bytes_per_launch"] * cells / e["cells"])
 
 
 def peaks():

@@ -123,6 +123,50 @@ struct Pool {
   }
 };
 
+// A second stream for codec work with a few events; on destruction the
+// owner's stream waits for everything issued on it (so stream-ordered frees
+// on the owner's stream stay safe on every return path).
+struct CodecStream {
+  cudaStream_t owner;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev[8] = {nullptr};
+  cudaEvent_t done = nullptr;
+  bool ok = false;
+  explicit CodecStream(cudaStream_t o) : owner(o) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    for (auto& e : ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+      }
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    // codec work may only start after everything the owner issued so far
+    ok = cudaEventRecord(done, owner) == cudaSuccess && cudaStreamWaitEvent(s, done, 0) == cudaSuccess;
+  }
+  // owner waits for all codec work issued so far
+  cudaError_t join() {
+    cudaError_t e = cudaEventRecord(done, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamWaitEvent(owner, done, 0);
+  }
+  ~CodecStream() {
+    if (s) {
+      join();
+      cudaStreamDestroy(s);
+    }
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    if (done) cudaEventDestroy(done);
+    cudaGetLastError();
+  }
+};
+
 bool geometry_ok(const fwi_geometry* g) {
   return g && g->nx > 0 && g->ny > 0 && g->nz > 0 && g->nt >= 0 && g->h > 0 && g->dt > 0 &&
          g->nbl >= 0 && (g->nbl == 0 || (g->sponge_R > 0 && g->sponge_R < 1 && g->vmax > 0)) &&
@@ -430,55 +474,97 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
   CK(cudaMemsetAsync(sizes, 0, sizeof(unsigned long long) * (nslots + 1), s));
   const int minexp = lossy ? minexp_of(pol->atol) : 0;
 
+  // Codec work runs on a second stream so that compressing u^{n+1} overlaps
+  // the next stencil step (which only reads that buffer) and decoding u^{k-1}
+  // overlaps adjoint step k.  Per-buffer events order every overwrite after
+  // the codec reads or writes that buffer.
+  CodecStream cs(s);
+  if (!cs.ok) return FWI_ERR_CUDA;
   auto store_field = [&](const float* f, int j) -> int {
     if (lossy) {
-      k_slot_offset<<<1, 1, 0, s>>>(offs, sizes, j);
+      k_slot_offset<<<1, 1, 0, cs.s>>>(offs, sizes, j);
       count_launch();
       CK(cudaGetLastError());
       CK(zfp_encode_launch(f, G, minexp, store->arena, offs + j, store->capacity, sizes + j,
-                           sw.d_status, scratch, s));
+                           sw.d_status, scratch, cs.s));
     } else {
-      CK(cudaMemcpyAsync(store->arena + (size_t)j * raw_slot, f, fbytes, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(store->arena + (size_t)j * raw_slot, f, fbytes, cudaMemcpyDeviceToDevice, cs.s));
     }
     return FWI_OK;
   };
-  auto load_field = [&](int j, float* f) -> int {
+  auto load_field = [&](int j, float* f, cudaStream_t st) -> int {
     if (lossy) {
-      CK(zfp_decode_launch(store->arena, offs + j, store->capacity, f, G, sw.d_status, s));
+      CK(zfp_decode_launch(store->arena, offs + j, store->capacity, f, G, sw.d_status, st));
     } else {
-      CK(cudaMemcpyAsync(f, store->arena + (size_t)j * raw_slot, fbytes, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(f, store->arena + (size_t)j * raw_slot, fbytes, cudaMemcpyDeviceToDevice, st));
     }
     return FWI_OK;
   };
+  // forward-state buffers: "encoded" events guard their reuse
+  float* fbuf[2] = {fprev, fcur};
+  cudaEvent_t f_read[2] = {cs.ev[0], cs.ev[1]};
+  bool f_pending[2] = {false, false};
+  auto fidx = [&](const float* p) { return p == fbuf[0] ? 0 : 1; };
+  // full-history decode double buffer
+  float* dbuf[2] = {rprev, ring[0]};
+  cudaEvent_t d_ready[2] = {cs.ev[2], cs.ev[3]}, d_used[2] = {cs.ev[4], cs.ev[5]};
+  bool d_issued[2] = {false, false}, d_inuse[2] = {false, false};
+  int d_step[2] = {-1, -1};
+  const bool full = pol->mode == FWI_CKPT_FULL;
+  auto issue_decode = [&](int k) -> int {  // full history: u^k into dbuf[k & 1] on the codec stream
+    const int b = k & 1;
+    if (d_inuse[b]) CK(cudaStreamWaitEvent(cs.s, d_used[b], 0));
+    if ((st = load_field(slot[{k, 1}], dbuf[b], cs.s))) return st;
+    CK(cudaEventRecord(d_ready[b], cs.s));
+    d_issued[b] = true;
+    d_step[b] = k;
+    return FWI_OK;
+  };
+  cudaEvent_t ev_adv = cs.ev[6];
 
   std::vector<float*> avail(N + 2, nullptr);
   int seg_c = 0;
   bool resid_ready = false;
   for (const fwi_action& a : sc.a) {
     switch (a.kind) {
-      case FWI_ACT_ADVANCE:
+      case FWI_ACT_ADVANCE: {
+        const int w = fidx(fprev);  // the step overwrites fprev
+        if (f_pending[w]) CK(cudaStreamWaitEvent(s, f_read[w], 0));
+        f_pending[w] = false;
         CK(stencil_step_launch(sw.sp, fcur, fprev, fprev, sw.src, sw.d_wavelet, a.step, s));
         std::swap(fprev, fcur);
         CK(gather_launch(fcur, sw.rec_cell, nrec, dsim + (size_t)a.step * nrec, s));
         break;
+      }
       case FWI_ACT_STORE:
         if (a.step > 0) {
+          CK(cudaEventRecord(ev_adv, s));
+          CK(cudaStreamWaitEvent(cs.s, ev_adv, 0));
           if ((st = store_field(fcur, slot[{a.step, 1}]))) return st;
           if (a.arg == 2 && (st = store_field(fprev, slot[{a.step, 0}]))) return st;
+          CK(cudaEventRecord(f_read[fidx(fcur)], cs.s));
+          f_pending[fidx(fcur)] = true;
+          if (a.arg == 2) {
+            CK(cudaEventRecord(f_read[fidx(fprev)], cs.s));
+            f_pending[fidx(fprev)] = true;
+          }
         }
         break;
       case FWI_ACT_RESTORE:
-        if (a.arg == 1) {  // full history: u^k into the decode buffer
-          if ((st = load_field(slot[{a.step, 1}], rprev))) return st;
-          avail[a.step] = rprev;
-        } else {           // state pair at the segment start
+        if (a.arg == 1) {  // full history: u^k (decoded ahead on the codec stream)
+          const int b = a.step & 1;
+          if (!(d_issued[b] && d_step[b] == a.step)) {
+            if ((st = issue_decode(a.step))) return st;
+          }
+        } else {           // state pair at the segment start (on the main stream)
+          CK(cs.join());
           seg_c = a.step;
           if (a.step == 0) {
             CK(cudaMemsetAsync(rprev, 0, fbytes, s));
             CK(cudaMemsetAsync(ring[0], 0, fbytes, s));
           } else {
-            if ((st = load_field(slot[{a.step, 0}], rprev))) return st;
-            if ((st = load_field(slot[{a.step, 1}], ring[0]))) return st;
+            if ((st = load_field(slot[{a.step, 0}], rprev, s))) return st;
+            if ((st = load_field(slot[{a.step, 1}], ring[0], s))) return st;
           }
           avail[a.step] = ring[0];
         }
@@ -493,13 +579,27 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
       case FWI_ACT_ADJOINT: {
         const int k = a.step;
         if (!resid_ready) {
+          CK(cs.join());  // every checkpoint is stored before the reverse sweep
           CK(misfit_launch(dsim, d_obs, (size_t)N * nrec, dsim, d_phi, d_part, s));
           resid_ready = true;
         }
-        if (!avail[k]) return FWI_ERR_ARG;
-        CK(stencil_adjoint_launch(sw.sp, lcur, lnext, lnext, avail[k], gacc, s));
+        const float* uk = avail[k];
+        int b = -1;
+        if (full) {
+          b = k & 1;
+          if (!(d_issued[b] && d_step[b] == k)) return FWI_ERR_ARG;
+          CK(cudaStreamWaitEvent(s, d_ready[b], 0));
+          uk = dbuf[b];
+          if (k > 1 && (st = issue_decode(k - 1))) return st;  // overlaps this step
+        }
+        if (!uk) return FWI_ERR_ARG;
+        CK(stencil_adjoint_launch(sw.sp, lcur, lnext, lnext, uk, gacc, s));
         CK(inject_adjoint_launch(sw.sp, sw.rec_cell, sw.rec_fac, nrec, dsim + (size_t)(k - 1) * nrec,
-                                 lnext, avail[k], gacc, s));
+                                 lnext, uk, gacc, s));
+        if (full) {
+          CK(cudaEventRecord(d_used[b], s));
+          d_inuse[b] = true;
+        }
         std::swap(lcur, lnext);  // lcur = l_{k-1}, lnext = l_k
         avail[k] = nullptr;
         break;
@@ -508,6 +608,7 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
         return FWI_ERR_ARG;
     }
   }
+  CK(cs.join());
   unsigned long long* d_end = sizes + nslots;
   if (lossy) {
     k_end_offset<<<1, 1, 0, s>>>(offs, sizes, nslots, d_end);
