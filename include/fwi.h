@@ -65,9 +65,18 @@ typedef struct {
 #define FWI_CKPT_EVERY_K 2 /* keep the pair (u^{c-1}, u^c) at c = 0, K, 2K, ...;
                               recompute the states in between during the
                               reverse sweep */
+#define FWI_CKPT_BINOMIAL 3 /* at most k_or_snaps state pairs at a time, placed by
+                               recursive splitting so that the forward steps
+                               recomputed are the fewest possible (the
+                               Revolve family of schedules, Sec. 1.2); the
+                               pairs are used last-in first-out */
+#define FWI_CKPT_SUBSAMPLE 4 /* the subsampling baseline of Sec. 4.7: keep u^k only for
+                                k = f, 2f, ... (f = k_or_snaps) and apply the imaging
+                                condition only at those steps, weighted by f */
 typedef struct {
   int mode;       /* FWI_CKPT_* */
-  int k_or_snaps; /* K for FWI_CKPT_EVERY_K, ignored otherwise */
+  int k_or_snaps; /* K for FWI_CKPT_EVERY_K, snapshot pairs for FWI_CKPT_BINOMIAL,
+                     the factor f for FWI_CKPT_SUBSAMPLE */
   double atol;    /* > 0: compress every checkpoint with this absolute error
                      tolerance (Sec. 1.3); <= 0: raw FP32 copies */
 } fwi_ckpt_policy;
@@ -78,7 +87,9 @@ typedef struct {
 #define FWI_ACT_STORE 2     /* store the state at `step` (arg = 1: u^step; 2: u^{step-1}, u^step) */
 #define FWI_ACT_RESTORE 3   /* make the stored state at `step` current (arg as for STORE) */
 #define FWI_ACT_RECOMPUTE 4 /* forward step without recording: u^step -> u^{step+1} */
-#define FWI_ACT_ADJOINT 5   /* adjoint step k = step (lambda_{k-1}) and imaging with u^k */
+#define FWI_ACT_ADJOINT 5   /* adjoint step k = step (lambda_{k-1}) and imaging with u^k
+                               weighted by arg (0 means 1; -1: no imaging) */
+#define FWI_ACT_FREE 6      /* drop the most recently stored state pair (binomial) */
 typedef struct {
   int kind;
   int step;
@@ -137,6 +148,25 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
                  int src_j, int src_k, const int* d_rec_ijk, int nrec, const float* d_obs,
                  float* d_grad, double* h_misfit, fwi_ckpt_store* st,
                  const fwi_ckpt_policy* pol, void* stream);
+
+/* The two halves of fwi_gradient, for callers that form the adjoint source
+ * themselves (automatic differentiation: the forward pass keeps the
+ * checkpoints, the backward pass receives dL/dd for any loss L).
+ * fwi_forward_store runs the forward sweep, writes the records
+ * (d_rec_out[n*nrec + r] = u^{n+1}) and stores the checkpoints per pol in st
+ * (FWI_ERR_CAPACITY as for fwi_gradient).  fwi_adjoint_store then runs the
+ * reverse sweep from those checkpoints with the adjoint source d_resid
+ * (nt*nrec) injected at the receivers and accumulates
+ *   d_grad += -sum_k u^k (l_{k-1} - 2 l_k + l_{k+1}) / dt^2 = J^T d_resid
+ * (Eq. (4), J = dd/dm).  It needs the same geometry, policy, model,
+ * wavelet and acquisition as the forward call (FWI_ERR_ARG if the store holds
+ * no checkpoints from a matching forward call).  Both synchronise. */
+int fwi_forward_store(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
+                      int src_j, int src_k, const int* d_rec_ijk, int nrec, float* d_rec_out,
+                      fwi_ckpt_store* st, const fwi_ckpt_policy* pol, void* stream);
+int fwi_adjoint_store(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
+                      int src_j, int src_k, const int* d_rec_ijk, int nrec, const float* d_resid,
+                      float* d_grad, fwi_ckpt_store* st, const fwi_ckpt_policy* pol, void* stream);
 
 /* The same gradient with every array in host memory (h_m, h_rec_ijk, h_obs,
  * h_grad: same layouts as above; pinned memory gives the fastest copies).

@@ -25,8 +25,8 @@ _lock = threading.Lock()
 _lib = None
 
 OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_NONFINITE = 0, -1, -2, -3, -4
-CKPT_FULL, CKPT_EVERY_K = 1, 2
-ACT_ADVANCE, ACT_STORE, ACT_RESTORE, ACT_RECOMPUTE, ACT_ADJOINT = 1, 2, 3, 4, 5
+CKPT_FULL, CKPT_EVERY_K, CKPT_BINOMIAL, CKPT_SUBSAMPLE = 1, 2, 3, 4
+ACT_ADVANCE, ACT_STORE, ACT_RESTORE, ACT_RECOMPUTE, ACT_ADJOINT, ACT_FREE = 1, 2, 3, 4, 5, 6
 
 
 def build(force: bool = False) -> str:
@@ -93,6 +93,8 @@ def lib():
             L.oracle_zfp_perm.argtypes = [ip]
             L.oracle_zfp_block_quantise.argtypes = [fp, C.c_int, C.POINTER(C.c_int32), ip, ip]
             L.oracle_num_threads.restype = C.c_int
+            L.oracle_binomial_cost.argtypes = [C.c_int, C.c_int]
+            L.oracle_binomial_cost.restype = C.c_longlong
             _lib = L
     return _lib
 
@@ -182,6 +184,10 @@ def gradient(g, m, wavelet, src, rec, d_obs, mode=CKPT_FULL, k=1, atol=0.0, m0=N
     if st:
         raise RuntimeError(f"oracle_gradient failed: {st}")
     return grad, phi.value, dsim, nbytes.value
+
+
+def binomial_cost(n, s):
+    return int(lib().oracle_binomial_cost(n, s))
 
 
 def ckpt_schedule(nt, mode, k=1, atol=0.0):

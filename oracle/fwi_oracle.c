@@ -195,6 +195,86 @@ static void oc_emit(oracle_action* out, size_t cap, size_t* n, int kind, int ste
   (*n)++;
 }
 
+/* Binomial cost table cost[n][s], n = 0..N, s = 0..S (plain dynamic
+ * programming over the split point). */
+static long long* oc_binomial_table(int N, int S) {
+  long long* c = (long long*)malloc(sizeof(long long) * (size_t)(N + 1) * (S + 1));
+  for (int n = 0; n <= N; n++)
+    for (int s = 0; s <= S; s++) {
+      long long best = (long long)n * (n + 1) / 2;
+      if (s > 0)
+        for (int m = 1; m < n; m++) {
+          long long v = m + c[(size_t)(n - m) * (S + 1) + (s - 1)] + c[(size_t)m * (S + 1) + s];
+          if (v < best) best = v;
+        }
+      c[(size_t)n * (S + 1) + s] = best;
+    }
+  return c;
+}
+
+long long oracle_binomial_cost(int n, int s) {
+  if (n < 0 || s < 0) return -1;
+  long long* c = oc_binomial_table(n, s);
+  long long v = c[(size_t)n * (s + 1) + s];
+  free(c);
+  return v;
+}
+
+typedef struct {
+  oracle_action* out;
+  size_t cap, n;
+  const long long* cost;
+  int S;
+  int state;    /* step of the current forward state */
+  int advanced; /* steps 0 .. advanced-1 have been run once (recorded) */
+} oc_binom;
+
+static void oc_advance_to(oc_binom* b, int target) {
+  while (b->state < target) {
+    int kind = b->state >= b->advanced ? ORACLE_ACT_ADVANCE : ORACLE_ACT_RECOMPUTE;
+    oc_emit(b->out, b->cap, &b->n, kind, b->state, 0);
+    b->state++;
+    if (b->state > b->advanced) b->advanced = b->state;
+  }
+}
+
+/* serve adjoint steps a+n .. a+1, the state at a being stored, s spare slots */
+static void oc_binom_gen(oc_binom* b, int a, int n, int s) {
+  if (n <= 0) return;
+  long long base = (long long)n * (n + 1) / 2;
+  int m_best = 0;
+  if (s > 0) {
+    long long best = base;
+    for (int m = 1; m < n; m++) {
+      long long v = m + b->cost[(size_t)(n - m) * (b->S + 1) + (s - 1)] + b->cost[(size_t)m * (b->S + 1) + s];
+      if (v < best) {
+        best = v;
+        m_best = m;
+      }
+    }
+  }
+  if (m_best == 0) {
+    for (int k = a + n; k > a; k--) {
+      if (b->state != a) {
+        oc_emit(b->out, b->cap, &b->n, ORACLE_ACT_RESTORE, a, 2);
+        b->state = a;
+      }
+      oc_advance_to(b, k);
+      oc_emit(b->out, b->cap, &b->n, ORACLE_ACT_ADJOINT, k, 0);
+    }
+    return;
+  }
+  if (b->state != a) {
+    oc_emit(b->out, b->cap, &b->n, ORACLE_ACT_RESTORE, a, 2);
+    b->state = a;
+  }
+  oc_advance_to(b, a + m_best);
+  oc_emit(b->out, b->cap, &b->n, ORACLE_ACT_STORE, a + m_best, 2);
+  oc_binom_gen(b, a + m_best, n - m_best, s - 1);
+  oc_emit(b->out, b->cap, &b->n, ORACLE_ACT_FREE, a + m_best, 2);
+  oc_binom_gen(b, a, m_best, s);
+}
+
 int oracle_ckpt_schedule(int nt, const oracle_policy* pol, oracle_action* out, size_t cap,
                          size_t* n_out) {
   if (!pol || nt < 0 || !n_out) return ORACLE_ERR_ARG;
@@ -229,6 +309,31 @@ int oracle_ckpt_schedule(int nt, const oracle_policy* pol, oracle_action* out, s
       for (int s = c; s < e; s++) oc_emit(out, cap, &n, ORACLE_ACT_RECOMPUTE, s, 0);
       for (int k = e; k >= lo; k--) oc_emit(out, cap, &n, ORACLE_ACT_ADJOINT, k, 0);
     }
+  } else if (pol->mode == ORACLE_CKPT_SUBSAMPLE) {
+    /* subsampled imaging (Sec. 4.7): states kept only at multiples of f */
+    int f = pol->k;
+    if (f < 1) return ORACLE_ERR_ARG;
+    for (int s = 0; s < nt; s++) {
+      oc_emit(out, cap, &n, ORACLE_ACT_ADVANCE, s, 0);
+      if ((s + 1) % f == 0) oc_emit(out, cap, &n, ORACLE_ACT_STORE, s + 1, 1);
+    }
+    for (int k = nt; k >= 1; k--) {
+      if (k % f == 0) {
+        oc_emit(out, cap, &n, ORACLE_ACT_RESTORE, k, 1);
+        oc_emit(out, cap, &n, ORACLE_ACT_ADJOINT, k, f);
+      } else {
+        oc_emit(out, cap, &n, ORACLE_ACT_ADJOINT, k, -1);
+      }
+    }
+  } else if (pol->mode == ORACLE_CKPT_BINOMIAL) {
+    if (pol->k < 0) return ORACLE_ERR_ARG;
+    /* the zero state before the first step is the bottom snapshot */
+    oc_emit(out, cap, &n, ORACLE_ACT_STORE, 0, 2);
+    long long* cost = oc_binomial_table(nt, pol->k);
+    oc_binom b = {out, cap, n, cost, pol->k, 0, 0};
+    oc_binom_gen(&b, 0, nt, pol->k);
+    n = b.n;
+    free(cost);
   } else {
     return ORACLE_ERR_ARG;
   }
@@ -341,7 +446,7 @@ int oracle_gradient(const oracle_geometry* g, const double* m, const double* m0,
       state_step = s + 1;
       if (kind == ORACLE_ACT_ADVANCE) {
         for (int r = 0; r < nrec; r++) dsim[(long)s * nrec + r] = cur[rc[r]];
-      } else {
+      } else if (pol->mode != ORACLE_CKPT_BINOMIAL) {
         avail[s + 1] = (double*)malloc(sizeof(double) * C);
         memcpy(avail[s + 1], cur, sizeof(double) * C);
       }
@@ -357,10 +462,13 @@ int oracle_gradient(const oracle_geometry* g, const double* m, const double* m0,
         if (!st) st = oc_load(g, &saved_cur[s], cur);
         state_step = s;
       }
-      if (!st && s >= 1) {
+      if (!st && s >= 1 && pol->mode != ORACLE_CKPT_BINOMIAL) {
         avail[s] = (double*)malloc(sizeof(double) * C);
         st = oc_load(g, &saved_cur[s], avail[s]);
       }
+    } else if (kind == ORACLE_ACT_FREE) {
+      oc_free_saved(&saved_cur[s]);
+      oc_free_saved(&saved_prev[s]);
     } else if (kind == ORACLE_ACT_ADJOINT) {
       int k = s;
       if (!residual_ready) {
@@ -373,14 +481,22 @@ int oracle_gradient(const oracle_geometry* g, const double* m, const double* m0,
         *misfit = phi;
         residual_ready = 1;
       }
-      if (!avail[k]) { st = ORACLE_ERR_ARG; break; }
-      oc_step(g, m, sig, lcur, lnext, lnew, Lb, rc, resid + (long)(k - 1) * nrec, nrec);
+      /* binomial schedules image with the current forward state; the
+       * action's weight scales the imaging term (-1: none) */
+      const int weight = act[a].arg == 0 ? 1 : act[a].arg;
       const double* uk = avail[k];
+      if (pol->mode == ORACLE_CKPT_BINOMIAL) uk = state_step == k ? cur : NULL;
+      if (!uk && weight > 0) { st = ORACLE_ERR_ARG; break; }
+      oc_step(g, m, sig, lcur, lnext, lnew, Lb, rc, resid + (long)(k - 1) * nrec, nrec);
+      if (weight > 0) {
 #pragma omp parallel for schedule(static)
-      for (long i = 0; i < C; i++) grad[i] -= uk[i] * (lnew[i] - 2.0 * lcur[i] + lnext[i]) * idt2;
+        for (long i = 0; i < C; i++) grad[i] -= weight * uk[i] * (lnew[i] - 2.0 * lcur[i] + lnext[i]) * idt2;
+      }
       double* t = lnext; lnext = lcur; lcur = lnew; lnew = t;
-      free(avail[k]);
-      avail[k] = NULL;
+      if (pol->mode != ORACLE_CKPT_BINOMIAL) {
+        free(avail[k]);
+        avail[k] = NULL;
+      }
     }
   }
   if (!residual_ready && !st) { /* N = 0 */

@@ -58,6 +58,8 @@ typedef struct {
  * stores fixed-accuracy compressed FP32 copies (Sec. 1.3). */
 #define ORACLE_CKPT_FULL 1    /* keep u^k for every k = 1..N */
 #define ORACLE_CKPT_EVERY_K 2 /* keep (u^{c-1}, u^c) for c = 0, K, 2K, ... */
+#define ORACLE_CKPT_BINOMIAL 3 /* at most k state pairs at a time, placed to minimise recomputation */
+#define ORACLE_CKPT_SUBSAMPLE 4 /* keep u^k only for k = f, 2f, ...; image only there, weight f */
 typedef struct {
   int mode;
   int k;
@@ -70,7 +72,9 @@ typedef struct {
 #define ORACLE_ACT_STORE 2   /* store checkpoint at step (arg = levels: 1 or 2) */
 #define ORACLE_ACT_RESTORE 3 /* restore checkpoint at step */
 #define ORACLE_ACT_RECOMPUTE 4 /* forward step without recording: u^{step} -> u^{step+1} */
-#define ORACLE_ACT_ADJOINT 5 /* adjoint step k = step: lambda_{k-1} and imaging with u^k */
+#define ORACLE_ACT_ADJOINT 5 /* adjoint step k = step: lambda_{k-1}; imaging with u^k weighted by
+                                arg (0 means 1; -1: no imaging) */
+#define ORACLE_ACT_FREE 6    /* drop the most recent stored state (binomial schedules) */
 typedef struct {
   int kind;
   int step;
@@ -125,8 +129,16 @@ int oracle_gradient(const oracle_geometry* g, const double* m, const double* m0,
                     double* d_sim_out, double* ckpt_bytes_out);
 
 /* Checkpoint schedule for the policy: the ordered list of actions that
- * oracle_gradient executes.  Returns ORACLE_ERR_CAPACITY (and the needed count
- * in *n_out) when cap is too small. */
+ * oracle_gradient executes.  Binomial: with the state at a stored and s more
+ * snapshot slots, serving adjoint steps a+n .. a+1 costs
+ *   cost(n, 0) = n(n+1)/2 (restart from a for every step),
+ *   cost(n, s) = min(cost(n, 0), min_{0<m<n} m + cost(n-m, s-1) + cost(m, s)),
+ * the recursive splitting of Sec. 1.2's Revolve-family schedules; the
+ * smallest minimising m is taken.  Pinned: the table equals Griewank's
+ * closed-form minimum and the schedule's raw result equals full history. */
+long long oracle_binomial_cost(int n, int s);
+/* Returns ORACLE_ERR_CAPACITY (and the needed count in *n_out) when cap is
+ * too small. */
 int oracle_ckpt_schedule(int nt, const oracle_policy* pol, oracle_action* out,
                          size_t cap, size_t* n_out);
 

@@ -8,8 +8,10 @@ accumulates the imaging condition.  The compute path is the C-ABI CUDA
 library ``libfwi.so`` (include/fwi.h); this package binds it.
 """
 from .api import (  # noqa: F401
+    FWI_CKPT_BINOMIAL,
     FWI_CKPT_EVERY_K,
     FWI_CKPT_FULL,
+    FWI_CKPT_SUBSAMPLE,
     CheckpointStore,
     FwiError,
     Geometry,

@@ -14,8 +14,9 @@ LIB_PATH = os.path.join(HERE, "libfwi.so")
 
 FWI_OK, FWI_ERR_ARG, FWI_ERR_CAPACITY, FWI_ERR_CORRUPT = 0, -1, -2, -3
 FWI_ERR_NONFINITE, FWI_ERR_CUDA, FWI_ERR_TIMEOUT, FWI_ERR_NOMEM = -4, -5, -6, -7
-FWI_CKPT_FULL, FWI_CKPT_EVERY_K = 1, 2
-FWI_ACT_ADVANCE, FWI_ACT_STORE, FWI_ACT_RESTORE, FWI_ACT_RECOMPUTE, FWI_ACT_ADJOINT = 1, 2, 3, 4, 5
+FWI_CKPT_FULL, FWI_CKPT_EVERY_K, FWI_CKPT_BINOMIAL, FWI_CKPT_SUBSAMPLE = 1, 2, 3, 4
+FWI_ACT_ADVANCE, FWI_ACT_STORE, FWI_ACT_RESTORE, FWI_ACT_RECOMPUTE, FWI_ACT_ADJOINT, FWI_ACT_FREE = (
+    1, 2, 3, 4, 5, 6)
 
 #: every symbol include/fwi.h declares
 EXPORTS = [
@@ -23,7 +24,8 @@ EXPORTS = [
     "fwi_forward", "fwi_gradient", "fwi_gradient_host", "zfp_max_compressed_bytes",
     "zfp_compress_fixed_accuracy", "zfp_decompress", "fwi_misfit", "fwi_dot_f64",
     "fwi_status_string", "fwi_kernel_launch_count", "fwi_profile_enable", "fwi_profile_reset",
-    "fwi_profile_read", "zfp_compress_fixed_accuracy_noalloc",
+    "fwi_profile_read", "zfp_compress_fixed_accuracy_noalloc", "fwi_forward_store",
+    "fwi_adjoint_store",
 ]
 KERNEL_CLASSES = ["stencil_forward", "stencil_adjoint_imaging", "zfp_encode", "zfp_decode", "other"]
 
@@ -77,6 +79,9 @@ def load() -> C.CDLL:
         L.fwi_gradient.argtypes = [gp, fp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, fp, fp, dp,
                                    vp, pp, vp]
         L.fwi_gradient_host.argtypes = L.fwi_gradient.argtypes
+        L.fwi_forward_store.argtypes = [gp, fp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, fp, vp, pp, vp]
+        L.fwi_adjoint_store.argtypes = [gp, fp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, fp, fp, vp, pp,
+                                        vp]
         L.zfp_max_compressed_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
         L.zfp_max_compressed_bytes.restype = C.c_size_t
         L.zfp_compress_fixed_accuracy.argtypes = [fp, C.c_int, C.c_int, C.c_int, C.c_double, vp,

@@ -13,7 +13,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import FWI_CKPT_EVERY_K, FWI_CKPT_FULL, FwiError, check  # noqa: F401
+from ._lib import (FWI_CKPT_BINOMIAL, FWI_CKPT_EVERY_K, FWI_CKPT_FULL, FWI_CKPT_SUBSAMPLE,  # noqa: F401
+                   FwiError, check)
 
 
 @dataclass
@@ -167,6 +168,39 @@ def gradient(geom: Geometry, m: torch.Tensor, wavelet, src, rec: torch.Tensor,
         _dev(grad, torch.float32, "grad"), C.byref(phi), store.handle, C.byref(pol), _stream())
     check("fwi_gradient", st)
     return grad, phi.value
+
+
+def forward_store(geom: Geometry, m: torch.Tensor, wavelet, src, rec: torch.Tensor,
+                  store: CheckpointStore, mode: int = FWI_CKPT_FULL, k: int = 1, atol: float = 0.0):
+    """fwi_forward_store: records (nt, nrec), checkpoints kept in `store`."""
+    w = _host_f32(wavelet)
+    nrec = rec.shape[0]
+    d = torch.empty((geom.nt, nrec), dtype=torch.float32, device=m.device)
+    pol = _lib.Policy(mode, k, atol)
+    g = geom.cstruct()
+    st = _lib.load().fwi_forward_store(
+        C.byref(g), _dev(m, torch.float32, "m"), w.ctypes.data, int(src[0]), int(src[1]), int(src[2]),
+        _dev(rec, torch.int32, "rec"), nrec, _dev(d, torch.float32, "d"), store.handle, C.byref(pol),
+        _stream())
+    check("fwi_forward_store", st)
+    return d
+
+
+def adjoint_store(geom: Geometry, m: torch.Tensor, wavelet, src, rec: torch.Tensor,
+                  resid: torch.Tensor, store: CheckpointStore, mode: int = FWI_CKPT_FULL, k: int = 1,
+                  atol: float = 0.0, grad: torch.Tensor | None = None):
+    """fwi_adjoint_store: grad += J^T resid from the checkpoints in `store`."""
+    w = _host_f32(wavelet)
+    if grad is None:
+        grad = torch.zeros(geom.shape, dtype=torch.float32, device=m.device)
+    pol = _lib.Policy(mode, k, atol)
+    g = geom.cstruct()
+    st = _lib.load().fwi_adjoint_store(
+        C.byref(g), _dev(m, torch.float32, "m"), w.ctypes.data, int(src[0]), int(src[1]), int(src[2]),
+        _dev(rec, torch.int32, "rec"), rec.shape[0], _dev(resid, torch.float32, "resid"),
+        _dev(grad, torch.float32, "grad"), store.handle, C.byref(pol), _stream())
+    check("fwi_adjoint_store", st)
+    return grad
 
 
 def gradient_host(geom: Geometry, m: np.ndarray, wavelet, src, rec: np.ndarray, d_obs: np.ndarray,

@@ -105,14 +105,15 @@ cudaError_t stencil_step_launch(const StencilParams& p, const float* cur, const 
                                 float* out, long src_cell, const float* d_wavelet, int n,
                                 cudaStream_t s);
 // Adjoint step with fused imaging:
-//   out = step(cur, prev);  grad -= uk * (out - 2 cur + prev) / dt^2
+//   out = step(cur, prev);  grad -= weight * uk * (out - 2 cur + prev) / dt^2
 // (receiver injection is added afterwards by inject_adjoint_launch).
 cudaError_t stencil_adjoint_launch(const StencilParams& p, const float* cur, const float* prev,
-                                   float* out, const float* uk, float* grad, cudaStream_t s);
-// out[rec] += r * fac; grad[rec] -= uk[rec] * r * fac / dt^2.
+                                   float* out, const float* uk, float* grad, float weight,
+                                   cudaStream_t s);
+// out[rec] += r * fac; if uk: grad[rec] -= weight * uk[rec] * r * fac / dt^2.
 cudaError_t inject_adjoint_launch(const StencilParams& p, const long* rec_cell, const float* rec_fac,
                                   int nrec, const float* resid_row, float* out, const float* uk,
-                                  float* grad, cudaStream_t s);
+                                  float* grad, float weight, cudaStream_t s);
 // fac[r] = b / (1 + s dt/2) at receiver r (injection weight).
 cudaError_t rec_fac_launch(const StencilParams& p, const long* rec_cell, int nrec, float* fac,
                            cudaStream_t s);

@@ -239,6 +239,83 @@ struct Sched {
   void add(int kind, int step, int arg) { a.push_back(fwi_action{kind, step, arg}); }
 };
 
+// Binomial checkpointing.  With the state at step a stored and s further
+// snapshot slots, serving adjoint steps a+n .. a+1 needs at least
+//   cost(n, s) = n + t(n, s+1)
+// forward steps, t(l, S) = r l - C(S+r, S+1) being Griewank's minimum for l
+// steps and S snapshots (r: the smallest r with C(S+r, S) >= l).  A split at
+// m costs m + cost(n-m, s-1) + cost(m, s); the smallest optimal m is used,
+// and with no spare slot every adjoint step restarts from a.  A stored state
+// is restored only when the current forward state is not already at a, so
+// data are always recorded from the exact first pass.
+struct Binomial {
+  Sched& out;
+  int state = 0;     // step of the current forward state
+  int advanced = 0;  // steps 0 .. advanced-1 ran once (recorded)
+  Binomial(Sched& o, int) : out(o) {}
+
+  static long long choose_capped(int n, int k, long long cap) {  // C(n, k), capped at cap + 1
+    if (k < 0 || k > n) return 0;
+    long long c = 1;
+    for (int i = 1; i <= k; ++i) {
+      c = c * (n - k + i) / i;
+      if (c > cap) return cap + 1;
+    }
+    return c;
+  }
+  static long long cost(int n, int s) {
+    if (n <= 0) return 0;
+    const int S = s + 1;
+    int r = 0;
+    while (choose_capped(S + r, S, n) < n) ++r;
+    // C(S+r, S+1) = C(S+r, r-1), a product of r-1 terms (exact at each step)
+    long long c = r >= 1 ? 1 : 0;
+    for (int i = 1; i <= r - 1; ++i) c = c * (S + 1 + i) / i;
+    return (long long)n + (long long)r * n - c;
+  }
+  void advance_to(int target) {
+    while (state < target) {
+      out.add(state >= advanced ? FWI_ACT_ADVANCE : FWI_ACT_RECOMPUTE, state, 0);
+      ++state;
+      if (state > advanced) advanced = state;
+    }
+  }
+  void restore(int a) {
+    if (state != a) {
+      out.add(FWI_ACT_RESTORE, a, 2);
+      state = a;
+    }
+  }
+  void reverse(int a, int n, int s) {
+    if (n <= 0) return;
+    int m_best = 0;
+    if (s > 0) {
+      long long best = (long long)n * (n + 1) / 2;
+      for (int m = 1; m < n; ++m) {
+        const long long v = m + cost(n - m, s - 1) + cost(m, s);
+        if (v < best) {
+          best = v;
+          m_best = m;
+        }
+      }
+    }
+    if (m_best == 0) {
+      for (int k = a + n; k > a; --k) {
+        restore(a);
+        advance_to(k);
+        out.add(FWI_ACT_ADJOINT, k, 0);
+      }
+      return;
+    }
+    restore(a);
+    advance_to(a + m_best);
+    out.add(FWI_ACT_STORE, a + m_best, 2);
+    reverse(a + m_best, n - m_best, s - 1);
+    out.add(FWI_ACT_FREE, a + m_best, 2);
+    reverse(a, m_best, s);
+  }
+};
+
 int make_schedule(int nt, const fwi_ckpt_policy* pol, Sched& out) {
   if (!pol || nt < 0) return FWI_ERR_ARG;
   if (pol->mode == FWI_CKPT_FULL) {
@@ -271,6 +348,30 @@ int make_schedule(int nt, const fwi_ckpt_policy* pol, Sched& out) {
     }
     return FWI_OK;
   }
+  if (pol->mode == FWI_CKPT_SUBSAMPLE) {  // imaging every f-th step only (Sec. 4.7)
+    const int f = pol->k_or_snaps;
+    if (f < 1) return FWI_ERR_ARG;
+    for (int s = 0; s < nt; ++s) {
+      out.add(FWI_ACT_ADVANCE, s, 0);
+      if ((s + 1) % f == 0) out.add(FWI_ACT_STORE, s + 1, 1);
+    }
+    for (int k = nt; k > 0; --k) {
+      if (k % f == 0) {
+        out.add(FWI_ACT_RESTORE, k, 1);
+        out.add(FWI_ACT_ADJOINT, k, f);
+      } else {
+        out.add(FWI_ACT_ADJOINT, k, -1);
+      }
+    }
+    return FWI_OK;
+  }
+  if (pol->mode == FWI_CKPT_BINOMIAL) {
+    if (pol->k_or_snaps < 0) return FWI_ERR_ARG;
+    out.add(FWI_ACT_STORE, 0, 2);  // the zero state before the first step
+    Binomial b(out, pol->k_or_snaps);
+    b.reverse(0, nt, pol->k_or_snaps);
+    return FWI_OK;
+  }
   return FWI_ERR_ARG;
 }
 
@@ -280,9 +381,10 @@ int make_schedule(int nt, const fwi_ckpt_policy* pol, Sched& out) {
 __global__ void k_slot_offset(unsigned long long* off, const unsigned long long* size, int j) {
   off[j] = j == 0 ? 0ull : off[j - 1] + ((size[j - 1] + 255ull) & ~255ull);
 }
-__global__ void k_end_offset(const unsigned long long* off, const unsigned long long* size, int n,
-                             unsigned long long* end) {
-  *end = n == 0 ? 0ull : off[n - 1] + ((size[n - 1] + 255ull) & ~255ull);
+__global__ void k_track_peak(const unsigned long long* off, const unsigned long long* size, int j,
+                             unsigned long long* peak) {
+  const unsigned long long e = off[j] + ((size[j] + 255ull) & ~255ull);
+  if (e > *peak) *peak = e;
 }
 
 }  // namespace
@@ -294,6 +396,15 @@ struct fwi_ckpt_store {
   uint8_t* arena = nullptr;
   size_t capacity = 0;
   fwi_store_stats stats{};
+  // slot table of the last forward sweep (device), kept for a later reverse sweep
+  unsigned long long* d_offs = nullptr;
+  unsigned long long* d_sizes = nullptr;
+  int slot_cap = 0;
+  bool filled = false;  // a forward sweep completed and its checkpoints are in the arena
+  float* carry = nullptr;  // binomial: final forward state pair kept between the two halves
+  size_t carry_bytes = 0;
+  fwi_geometry geom{};
+  fwi_ckpt_policy pol{};
 };
 
 extern "C" {
@@ -370,6 +481,8 @@ int fwi_ckpt_store_create(size_t capacity_bytes, fwi_ckpt_store** out) {
 int fwi_ckpt_store_destroy(fwi_ckpt_store* st) {
   if (!st) return FWI_ERR_ARG;
   if (st->arena) cudaFree(st->arena);
+  if (st->d_offs) cudaFree(st->d_offs);
+  if (st->carry) cudaFree(st->carry);
   delete st;
   return FWI_OK;
 }
@@ -413,14 +526,37 @@ int fwi_forward(const fwi_geometry* g, const float* d_m, const float* h_wavelet,
   return status_from_flags(flags);
 }
 
-int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
-                 int src_j, int src_k, const int* d_rec_ijk, int nrec, const float* d_obs,
-                 float* d_grad, double* h_misfit, fwi_ckpt_store* store,
-                 const fwi_ckpt_policy* pol, void* stream) {
+}  // extern "C"
+
+namespace {
+
+enum { PH_FWD = 1, PH_REV = 2 };
+
+bool same_run(const fwi_geometry& a, const fwi_geometry& b, const fwi_ckpt_policy& p,
+              const fwi_ckpt_policy& q) {
+  return a.nx == b.nx && a.ny == b.ny && a.nz == b.nz && a.h == b.h && a.dt == b.dt && a.nt == b.nt &&
+         a.nbl == b.nbl && a.sponge_R == b.sponge_R && a.vmax == b.vmax && p.mode == q.mode &&
+         p.k_or_snaps == q.k_or_snaps && p.atol == q.atol;
+}
+
+// The checkpointed sweeps.  PH_FWD: forward sweep recording data (into
+// d_rec_out, or an internal buffer) and storing checkpoints per the policy.
+// PH_REV: reverse sweep from the store's checkpoints with the adjoint source
+// d_resid (or, when both phases run, the residual d_sim - d_obs, whose misfit
+// goes to *h_misfit), accumulating d_grad += dPhi/dm.
+int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i, int src_j,
+               int src_k, const int* d_rec_ijk, int nrec, float* d_rec_out, const float* d_obs,
+               const float* d_resid, float* d_grad, double* h_misfit, fwi_ckpt_store* store,
+               const fwi_ckpt_policy* pol, void* stream, int phases) {
+  const bool do_fwd = phases & PH_FWD, do_rev = phases & PH_REV;
   if (!geometry_ok(g) || !d_m || (g->nt > 0 && !h_wavelet) || nrec < 0 ||
-      (nrec > 0 && (!d_rec_ijk || !d_obs)) || !d_grad || !h_misfit || !store || !pol ||
-      !in_grid(g, src_i, src_j, src_k))
+      (nrec > 0 && !d_rec_ijk) || !store || !pol || !in_grid(g, src_i, src_j, src_k))
     return FWI_ERR_ARG;
+  if (do_rev && !d_grad) return FWI_ERR_ARG;
+  if (do_fwd && do_rev && nrec > 0 && (!d_obs || !h_misfit)) return FWI_ERR_ARG;
+  if (!do_fwd && do_rev && nrec > 0 && !d_resid) return FWI_ERR_ARG;
+  if (do_fwd && !do_rev && nrec > 0 && !d_rec_out) return FWI_ERR_ARG;
+  if (!do_fwd && (!store->filled || !same_run(store->geom, *g, store->pol, *pol))) return FWI_ERR_ARG;
   Sched sc;
   int st = make_schedule(g->nt, pol, sc);
   if (st) return st;
@@ -443,10 +579,21 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
       slot[{a.step, 1}] = j;
       if (a.arg == 2) slot[{a.step, 0}] = j + 1;
     }
-  const int nslots = (int)slot.size();
+  const bool binom = pol->mode == FWI_CKPT_BINOMIAL;
+  const int nslots = binom ? 2 * pol->k_or_snaps : (int)slot.size();
   const size_t raw_slot = (fbytes + 255) / 256 * 256;
-  store->stats = fwi_store_stats{store->capacity, 0, (size_t)nslots * (size_t)G.nx * G.ny * G.nz * 4,
-                                 nslots, 0};
+  // forward phase: the actions before the first one that is neither ADVANCE nor STORE
+  size_t first_rev = sc.a.size();
+  for (size_t i = 0; i < sc.a.size(); ++i)
+    if (sc.a[i].kind != FWI_ACT_ADVANCE && sc.a[i].kind != FWI_ACT_STORE) {
+      first_rev = i;
+      break;
+    }
+  if (do_fwd) {
+    store->filled = false;
+    store->stats = fwi_store_stats{store->capacity, 0, (size_t)nslots * (size_t)G.nx * G.ny * G.nz * 4,
+                                   nslots, 0};
+  }
   if (!lossy && (size_t)nslots * raw_slot > store->capacity) {
     store->stats.used_bytes = (size_t)nslots * raw_slot;
     store->stats.overflowed = 1;
@@ -458,12 +605,23 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
   float* lnext = pool.get<float>(G.cells());
   float* lcur = pool.get<float>(G.cells());
   float* gacc = pool.get<float>(G.cells());
-  float* dsim = pool.get<float>((size_t)N * (nrec > 0 ? nrec : 1));
+  float* dsim = (do_fwd && do_rev) || !d_rec_out ? pool.get<float>((size_t)N * (nrec > 0 ? nrec : 1)) : d_rec_out;
   double* d_phi = pool.get<double>(1);
   double* d_part = pool.get<double>(reduce_scratch_doubles());
-  unsigned long long* offs = pool.get<unsigned long long>(nslots + 1);
-  unsigned long long* sizes = pool.get<unsigned long long>(nslots + 1);
-  void* scratch = lossy ? (void*)pool.get<unsigned char>(zfp_encode_scratch_bytes(G.nx, G.ny, G.nz)) : nullptr;
+  if (store->slot_cap < nslots + 1) {
+    if (store->d_offs) cudaFree(store->d_offs);
+    store->d_offs = nullptr;
+    store->slot_cap = 0;
+    if (cudaMalloc(&store->d_offs, sizeof(unsigned long long) * (2 * (nslots + 1) + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      return FWI_ERR_NOMEM;
+    }
+    store->slot_cap = nslots + 1;
+  }
+  unsigned long long* offs = store->d_offs;
+  unsigned long long* sizes = store->d_offs + store->slot_cap;
+  unsigned long long* d_peak = store->d_offs + 2 * store->slot_cap;  // largest arena end so far
+  void* scratch = lossy && do_fwd ? (void*)pool.get<unsigned char>(zfp_encode_scratch_bytes(G.nx, G.ny, G.nz)) : nullptr;
   const int K = pol->mode == FWI_CKPT_EVERY_K ? pol->k_or_snaps : 1;
   std::vector<float*> ring(K, nullptr);
   for (int i = 0; i < K; ++i) ring[i] = pool.get<float>(G.cells());
@@ -471,7 +629,8 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
   if (pool.failed) return FWI_ERR_NOMEM;
   for (float* f : {fprev, fcur, lnext, lcur, gacc, rprev}) CK(cudaMemsetAsync(f, 0, fbytes, s));
   CK(cudaMemsetAsync(d_phi, 0, sizeof(double), s));
-  CK(cudaMemsetAsync(sizes, 0, sizeof(unsigned long long) * (nslots + 1), s));
+  if (do_fwd) CK(cudaMemsetAsync(sizes, 0, sizeof(unsigned long long) * (store->slot_cap + 1), s));
+  if (do_fwd) CK(cudaMemsetAsync(d_peak, 0, sizeof(unsigned long long), s));
   const int minexp = lossy ? minexp_of(pol->atol) : 0;
 
   // Codec work runs on a second stream so that compressing u^{n+1} overlaps
@@ -487,6 +646,9 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
       CK(cudaGetLastError());
       CK(zfp_encode_launch(f, G, minexp, store->arena, offs + j, store->capacity, sizes + j,
                            sw.d_status, scratch, cs.s));
+      k_track_peak<<<1, 1, 0, cs.s>>>(offs, sizes, j, d_peak);
+      count_launch();
+      CK(cudaGetLastError());
     } else {
       CK(cudaMemcpyAsync(store->arena + (size_t)j * raw_slot, f, fbytes, cudaMemcpyDeviceToDevice, cs.s));
     }
@@ -510,9 +672,11 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
   cudaEvent_t d_ready[2] = {cs.ev[2], cs.ev[3]}, d_used[2] = {cs.ev[4], cs.ev[5]};
   bool d_issued[2] = {false, false}, d_inuse[2] = {false, false};
   int d_step[2] = {-1, -1};
-  const bool full = pol->mode == FWI_CKPT_FULL;
-  auto issue_decode = [&](int k) -> int {  // full history: u^k into dbuf[k & 1] on the codec stream
-    const int b = k & 1;
+  const bool full = pol->mode == FWI_CKPT_FULL || pol->mode == FWI_CKPT_SUBSAMPLE;
+  int next_buf = 0;
+  auto issue_decode = [&](int k) -> int {  // u^k into the next decode buffer, on the codec stream
+    const int b = next_buf;
+    next_buf ^= 1;
     if (d_inuse[b]) CK(cudaStreamWaitEvent(cs.s, d_used[b], 0));
     if ((st = load_field(slot[{k, 1}], dbuf[b], cs.s))) return st;
     CK(cudaEventRecord(d_ready[b], cs.s));
@@ -525,38 +689,87 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
   std::vector<float*> avail(N + 2, nullptr);
   int seg_c = 0;
   bool resid_ready = false;
-  for (const fwi_action& a : sc.a) {
+  int state_step = 0;          // step of the forward state held in (fprev, fcur)
+  std::vector<int> bstack;     // binomial: steps of the stored pairs, bottom first
+  auto bslot = [&](int depth, int level) { return 2 * depth + (level ? 0 : 1); };
+  if (binom && !do_fwd) {
+    // the reverse half starts where the forward half stopped: rebuild the
+    // snapshot stack and bring back the final state pair
+    for (size_t i = 0; i < first_rev; ++i)
+      if (sc.a[i].kind == FWI_ACT_STORE && sc.a[i].step > 0) bstack.push_back(sc.a[i].step);
+    if (!store->carry || store->carry_bytes < 2 * fbytes) return FWI_ERR_ARG;
+    CK(cudaMemcpyAsync(fprev, store->carry, fbytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(fcur, (uint8_t*)store->carry + fbytes, fbytes, cudaMemcpyDeviceToDevice, s));
+    state_step = N;
+  }
+  for (size_t ai = 0; ai < sc.a.size(); ++ai) {
+    const fwi_action& a = sc.a[ai];
+    if ((ai < first_rev && !do_fwd) || (ai >= first_rev && !do_rev)) continue;
+    if (ai == first_rev && do_fwd && !do_rev && binom) break;
     switch (a.kind) {
-      case FWI_ACT_ADVANCE: {
+      case FWI_ACT_ADVANCE:
+      case FWI_ACT_RECOMPUTE: {
+        if (a.kind == FWI_ACT_RECOMPUTE && !binom) {  // every-K: segment ring
+          const int i = a.step - seg_c;
+          const float* prev = i == 0 ? rprev : ring[i - 1];
+          CK(stencil_step_launch(sw.sp, ring[i], prev, ring[i + 1], sw.src, sw.d_wavelet, a.step, s));
+          avail[a.step + 1] = ring[i + 1];
+          break;
+        }
+        if (state_step != a.step) return FWI_ERR_ARG;
         const int w = fidx(fprev);  // the step overwrites fprev
         if (f_pending[w]) CK(cudaStreamWaitEvent(s, f_read[w], 0));
         f_pending[w] = false;
         CK(stencil_step_launch(sw.sp, fcur, fprev, fprev, sw.src, sw.d_wavelet, a.step, s));
         std::swap(fprev, fcur);
-        CK(gather_launch(fcur, sw.rec_cell, nrec, dsim + (size_t)a.step * nrec, s));
+        state_step = a.step + 1;
+        if (a.kind == FWI_ACT_ADVANCE)
+          CK(gather_launch(fcur, sw.rec_cell, nrec, dsim + (size_t)a.step * nrec, s));
         break;
       }
       case FWI_ACT_STORE:
         if (a.step > 0) {
+          if (state_step != a.step) return FWI_ERR_ARG;
           CK(cudaEventRecord(ev_adv, s));
           CK(cudaStreamWaitEvent(cs.s, ev_adv, 0));
-          if ((st = store_field(fcur, slot[{a.step, 1}]))) return st;
-          if (a.arg == 2 && (st = store_field(fprev, slot[{a.step, 0}]))) return st;
+          const int j1 = binom ? bslot((int)bstack.size(), 1) : slot[{a.step, 1}];
+          const int j0 = binom ? bslot((int)bstack.size(), 0) : (a.arg == 2 ? slot[{a.step, 0}] : -1);
+          if ((st = store_field(fcur, j1))) return st;
+          if (a.arg == 2 && (st = store_field(fprev, j0))) return st;
           CK(cudaEventRecord(f_read[fidx(fcur)], cs.s));
           f_pending[fidx(fcur)] = true;
           if (a.arg == 2) {
             CK(cudaEventRecord(f_read[fidx(fprev)], cs.s));
             f_pending[fidx(fprev)] = true;
           }
+          if (binom) bstack.push_back(a.step);
         }
         break;
+      case FWI_ACT_FREE:
+        if (!binom || bstack.empty() || bstack.back() != a.step) return FWI_ERR_ARG;
+        CK(cs.join());  // the slot's next user must not overtake the encode
+        bstack.pop_back();
+        break;
       case FWI_ACT_RESTORE:
-        if (a.arg == 1) {  // full history: u^k (decoded ahead on the codec stream)
-          const int b = a.step & 1;
-          if (!(d_issued[b] && d_step[b] == a.step)) {
+        if (a.arg == 1) {  // single state u^k (decoded ahead on the codec stream)
+          if (!(d_issued[0] && d_step[0] == a.step) && !(d_issued[1] && d_step[1] == a.step)) {
             if ((st = issue_decode(a.step))) return st;
           }
-        } else {           // state pair at the segment start (on the main stream)
+        } else if (binom) {  // the top snapshot pair becomes the forward state
+          CK(cs.join());
+          f_pending[0] = f_pending[1] = false;
+          if (a.step == 0) {
+            if (!bstack.empty()) return FWI_ERR_ARG;
+            CK(cudaMemsetAsync(fprev, 0, fbytes, s));
+            CK(cudaMemsetAsync(fcur, 0, fbytes, s));
+          } else {
+            if (bstack.empty() || bstack.back() != a.step) return FWI_ERR_ARG;
+            const int d = (int)bstack.size() - 1;
+            if ((st = load_field(bslot(d, 0), fprev, s))) return st;
+            if ((st = load_field(bslot(d, 1), fcur, s))) return st;
+          }
+          state_step = a.step;
+        } else {           // every-K: state pair at the segment start (on the main stream)
           CK(cs.join());
           seg_c = a.step;
           if (a.step == 0) {
@@ -569,33 +782,42 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
           avail[a.step] = ring[0];
         }
         break;
-      case FWI_ACT_RECOMPUTE: {
-        const int i = a.step - seg_c;
-        const float* prev = i == 0 ? rprev : ring[i - 1];
-        CK(stencil_step_launch(sw.sp, ring[i], prev, ring[i + 1], sw.src, sw.d_wavelet, a.step, s));
-        avail[a.step + 1] = ring[i + 1];
-        break;
-      }
       case FWI_ACT_ADJOINT: {
         const int k = a.step;
+        const int weight = a.arg == 0 ? 1 : a.arg;
         if (!resid_ready) {
-          CK(cs.join());  // every checkpoint is stored before the reverse sweep
-          CK(misfit_launch(dsim, d_obs, (size_t)N * nrec, dsim, d_phi, d_part, s));
+          CK(cs.join());  // every checkpoint of the first pass is stored
+          if (do_fwd) CK(misfit_launch(dsim, d_obs, (size_t)N * nrec, dsim, d_phi, d_part, s));
           resid_ready = true;
+        }
+        const float* resid = do_fwd ? dsim : d_resid;
+        if (weight < 0) {  // adjoint step without imaging (subsampled schedules)
+          CK(stencil_step_launch(sw.sp, lcur, lnext, lnext, -1, sw.d_wavelet, 0, s));
+          CK(inject_adjoint_launch(sw.sp, sw.rec_cell, sw.rec_fac, nrec, resid + (size_t)(k - 1) * nrec,
+                                   lnext, nullptr, gacc, 0.f, s));
+          std::swap(lcur, lnext);
+          break;
         }
         const float* uk = avail[k];
         int b = -1;
         if (full) {
-          b = k & 1;
-          if (!(d_issued[b] && d_step[b] == k)) return FWI_ERR_ARG;
+          b = (d_issued[0] && d_step[0] == k) ? 0 : ((d_issued[1] && d_step[1] == k) ? 1 : -1);
+          if (b < 0) return FWI_ERR_ARG;
           CK(cudaStreamWaitEvent(s, d_ready[b], 0));
           uk = dbuf[b];
-          if (k > 1 && (st = issue_decode(k - 1))) return st;  // overlaps this step
+          // decode the next stored state while this step runs
+          for (size_t nx = ai + 1; nx < sc.a.size(); ++nx)
+            if (sc.a[nx].kind == FWI_ACT_RESTORE) {
+              if ((st = issue_decode(sc.a[nx].step))) return st;
+              break;
+            }
+        } else if (binom) {
+          uk = state_step == k ? fcur : nullptr;
         }
         if (!uk) return FWI_ERR_ARG;
-        CK(stencil_adjoint_launch(sw.sp, lcur, lnext, lnext, uk, gacc, s));
-        CK(inject_adjoint_launch(sw.sp, sw.rec_cell, sw.rec_fac, nrec, dsim + (size_t)(k - 1) * nrec,
-                                 lnext, uk, gacc, s));
+        CK(stencil_adjoint_launch(sw.sp, lcur, lnext, lnext, uk, gacc, (float)weight, s));
+        CK(inject_adjoint_launch(sw.sp, sw.rec_cell, sw.rec_fac, nrec, resid + (size_t)(k - 1) * nrec,
+                                 lnext, uk, gacc, (float)weight, s));
         if (full) {
           CK(cudaEventRecord(d_used[b], s));
           d_inuse[b] = true;
@@ -608,22 +830,34 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
         return FWI_ERR_ARG;
     }
   }
-  CK(cs.join());
-  unsigned long long* d_end = sizes + nslots;
-  if (lossy) {
-    k_end_offset<<<1, 1, 0, s>>>(offs, sizes, nslots, d_end);
-    count_launch();
-    CK(cudaGetLastError());
+  if (binom && do_fwd && !do_rev) {
+    // keep the final forward state pair for the reverse half
+    if (store->carry_bytes < 2 * fbytes) {
+      if (store->carry) cudaFree(store->carry);
+      store->carry = nullptr;
+      store->carry_bytes = 0;
+      if (cudaMalloc(&store->carry, 2 * fbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return FWI_ERR_NOMEM;
+      }
+      store->carry_bytes = 2 * fbytes;
+    }
+    CK(cudaMemcpyAsync(store->carry, fprev, fbytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync((uint8_t*)store->carry + fbytes, fcur, fbytes, cudaMemcpyDeviceToDevice, s));
   }
+  CK(cs.join());
+  unsigned long long* d_end = d_peak;
   int flags = 0;
   double phi = 0.0;
   unsigned long long used = lossy ? 0ull : (unsigned long long)nslots * raw_slot;
   CK(cudaMemcpyAsync(&flags, sw.d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&phi, d_phi, sizeof(double), cudaMemcpyDeviceToHost, s));
-  if (lossy) CK(cudaMemcpyAsync(&used, d_end, sizeof(used), cudaMemcpyDeviceToHost, s));
+  if (lossy && do_fwd) CK(cudaMemcpyAsync(&used, d_end, sizeof(used), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  store->stats.used_bytes = (size_t)used;
-  store->stats.overflowed = (flags & ST_CAPACITY) ? 1 : 0;
+  if (do_fwd) {
+    store->stats.used_bytes = (size_t)used;
+    store->stats.overflowed = (flags & ST_CAPACITY) ? 1 : 0;
+  }
   if (flags) {
     if ((flags & ST_CORRUPT) && !(flags & ST_CAPACITY) && !(flags & ST_NONFINITE)) {
       // an out-of-range receiver also raises this flag during setup
@@ -631,10 +865,44 @@ int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet
     }
     return status_from_flags(flags);
   }
-  CK(unpack_add_launch(gacc, G, d_grad, s));
-  CK(cudaStreamSynchronize(s));
-  *h_misfit = phi;
+  if (do_fwd) {
+    store->filled = true;
+    store->geom = *g;
+    store->pol = *pol;
+  }
+  if (do_rev) {
+    CK(unpack_add_launch(gacc, G, d_grad, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (do_fwd && do_rev && h_misfit) *h_misfit = phi;
   return FWI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fwi_gradient(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
+                 int src_j, int src_k, const int* d_rec_ijk, int nrec, const float* d_obs,
+                 float* d_grad, double* h_misfit, fwi_ckpt_store* store,
+                 const fwi_ckpt_policy* pol, void* stream) {
+  if (!h_misfit || !d_grad) return FWI_ERR_ARG;
+  return run_sweeps(g, d_m, h_wavelet, src_i, src_j, src_k, d_rec_ijk, nrec, nullptr, d_obs, nullptr,
+                    d_grad, h_misfit, store, pol, stream, PH_FWD | PH_REV);
+}
+
+int fwi_forward_store(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
+                      int src_j, int src_k, const int* d_rec_ijk, int nrec, float* d_rec_out,
+                      fwi_ckpt_store* store, const fwi_ckpt_policy* pol, void* stream) {
+  return run_sweeps(g, d_m, h_wavelet, src_i, src_j, src_k, d_rec_ijk, nrec, d_rec_out, nullptr, nullptr,
+                    nullptr, nullptr, store, pol, stream, PH_FWD);
+}
+
+int fwi_adjoint_store(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
+                      int src_j, int src_k, const int* d_rec_ijk, int nrec, const float* d_resid,
+                      float* d_grad, fwi_ckpt_store* store, const fwi_ckpt_policy* pol, void* stream) {
+  return run_sweeps(g, d_m, h_wavelet, src_i, src_j, src_k, d_rec_ijk, nrec, nullptr, nullptr, d_resid,
+                    d_grad, nullptr, store, pol, stream, PH_REV);
 }
 
 int fwi_gradient_host(const fwi_geometry* g, const float* h_m, const float* h_wavelet, int src_i,

@@ -116,6 +116,25 @@ def layered_velocity(nx: int, ny: int, nz: int, seed: int = 0, nlayers: int = 12
     return out
 
 
+def add_anomalies(v: np.ndarray, seed: int = 0, n: int = 3, amplitude: float = 0.08,
+                  sigma_frac: float = 0.08) -> np.ndarray:
+    """v * (1 + sum_j a_j exp(-|x - x_j|^2 / 2 s^2)) with n Gaussian anomalies of
+    amplitude +-`amplitude` (alternating sign), centres uniform in the middle
+    half of the model, width s = sigma_frac * min(nx, ny, nz) cells."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = v.shape
+    s = sigma_frac * min(nx, ny, nz)
+    z = np.arange(nz, dtype=np.float32)[:, None, None]
+    y = np.arange(ny, dtype=np.float32)[None, :, None]
+    x = np.arange(nx, dtype=np.float32)[None, None, :]
+    out = np.ones_like(v, dtype=np.float32)
+    for j in range(n):
+        cz, cy, cx = (rng.uniform(0.25, 0.75) * d for d in (nz, ny, nx))
+        a = amplitude * (1 if j % 2 == 0 else -1)
+        out += a * np.exp(-((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) / (2 * s * s)).astype(np.float32)
+    return (v * out).astype(np.float32)
+
+
 def smooth(v: np.ndarray, sigma_cells: float) -> np.ndarray:
     """Gaussian-smoothed copy (the paper's starting model, Sec. 3)."""
     from scipy.ndimage import gaussian_filter

@@ -45,7 +45,10 @@ def test_status_strings(fwi_lib):
 
 
 @pytest.mark.parametrize("nt,mode,k", [(0, 1, 1), (7, 1, 1), (12, 2, 1), (12, 2, 5), (13, 2, 4),
-                                       (40, 2, 10), (5, 2, 9), (2286, 2, 10), (2286, 1, 1)])
+                                       (40, 2, 10), (5, 2, 9), (2286, 2, 10), (2286, 1, 1),
+                                       (0, 3, 2), (1, 3, 1), (10, 3, 2), (70, 3, 4), (40, 3, 0),
+                                       (333, 3, 7), (2286, 3, 12), (6, 4, 2), (200, 4, 3),
+                                       (17, 4, 5), (2286, 4, 8)])
 def test_schedule_matches_oracle(fwi_lib, oracle, nt, mode, k):
     from paper_2009_12623_gb300 import api
     assert api.ckpt_schedule(nt, mode, k) == oracle.ckpt_schedule(nt, mode, k)

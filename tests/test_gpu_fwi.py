@@ -131,6 +131,49 @@ def test_gradient_ragged_every_k(cuda, oracle):
     assert abs(phi - phiref) <= phi_tol(dsim, dsim - d_obs)
 
 
+@pytest.mark.parametrize("snaps", [1, 3, 8])
+def test_binomial_raw_bitwise_equals_full_history(cuda, two_layer, snaps):
+    """Binomial (Revolve-family) checkpointing with raw pairs is bitwise exact."""
+    shot, d_obs = two_layer
+    g_full, phi_full, _ = _grad(cuda, shot, d_obs, 1)
+    g_b, phi_b, stats = _grad(cuda, shot, d_obs, 3, k=snaps)
+    assert np.array_equal(g_full, g_b) and phi_full == phi_b
+    assert stats["n_checkpoints"] == 2 * snaps
+
+
+def test_binomial_compressed_tracks_oracle(cuda, oracle):
+    from paper_2009_12623_gb300 import synth
+    shot = _small_shot()
+    og = _og(oracle, shot.geom)
+    m = synth.slowness2(shot.v0).astype(np.float64)
+    w = shot.wavelet.astype(np.float64)
+    d_obs = oracle.forward(og, synth.slowness2(shot.v_true).astype(np.float64), w, shot.src, shot.rec)
+    g_raw, phi_raw, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs)
+    g_oz, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs, mode=3, k=4, atol=1e-6)
+    g_gz, phi_gz, stats = _grad(cuda, shot, d_obs, 3, k=4, atol=1e-6)
+    e_o, e_g = rel(g_oz, g_raw), rel(g_gz, g_raw)
+    assert e_g <= 1.5 * e_o + TOL, (e_g, e_o)
+    assert stats["used_bytes"] < stats["raw_bytes"] / 2
+
+
+def test_subsampling_matches_oracle(cuda, oracle):
+    """Subsampled imaging (Sec. 4.7) on the GPU: f = 1 is bitwise full history,
+    f = 4 follows the FP64 oracle's subsampled gradient."""
+    from paper_2009_12623_gb300 import synth
+    shot = _small_shot()
+    og = _og(oracle, shot.geom)
+    m = synth.slowness2(shot.v0).astype(np.float64)
+    w = shot.wavelet.astype(np.float64)
+    d_obs = oracle.forward(og, synth.slowness2(shot.v_true).astype(np.float64), w, shot.src, shot.rec)
+    g_full, *_ = _grad(cuda, shot, d_obs, 1)
+    g_s1, *_ = _grad(cuda, shot, d_obs, 4, k=1)
+    assert np.array_equal(g_full, g_s1)
+    g_o4, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs, mode=4, k=4)
+    g_g4, _, stats = _grad(cuda, shot, d_obs, 4, k=4)
+    assert rel(g_g4, g_o4) < TOL
+    assert stats["n_checkpoints"] == shot.geom.nt // 4
+
+
 @pytest.mark.parametrize("k", [1, 4, 10, 33, 500])
 def test_every_k_raw_bitwise_equals_full_history(cuda, two_layer, k):
     """Checkpointing alone is bitwise exact (Sec. 1.2) on the GPU too."""

@@ -146,3 +146,85 @@ def test_schedule_full_structure(oracle):
     acts = oracle.ckpt_schedule(5, oracle.CKPT_FULL)
     kinds = [a[0] for a in acts]
     assert kinds == [1, 2] * 5 + [3, 5] * 5
+
+
+def _griewank_min_steps(n, snaps):
+    """Griewank's minimal number of extra forward steps to reverse n steps with
+    `snaps` snapshots: r n - C(snaps + r, snaps + 1), r the repetition number
+    with C(snaps + r - 1, snaps) < n <= C(snaps + r, snaps)."""
+    from math import comb
+    r = 0
+    while comb(snaps + r, snaps) < n:
+        r += 1
+    return r * n - comb(snaps + r, snaps + 1)
+
+
+@pytest.mark.parametrize("n,s", [(1, 1), (5, 1), (10, 2), (37, 3), (100, 4), (257, 6), (300, 2)])
+def test_binomial_cost_is_griewank_minimum(oracle, n, s):
+    # s spare slots besides the stored start state: Griewank's count with s + 1
+    # snapshots, plus the n steps of the first pass
+    assert oracle.binomial_cost(n, s) == n + _griewank_min_steps(n, s + 1)
+
+
+@pytest.mark.parametrize("nt,s", [(1, 1), (10, 2), (25, 3), (70, 4), (40, 0)])
+def test_binomial_schedule_structure(oracle, nt, s):
+    acts = oracle.ckpt_schedule(nt, oracle.CKPT_BINOMIAL, s)
+    assert [st for kind, st, _ in acts if kind == oracle.ACT_ADJOINT] == list(range(nt, 0, -1))
+    assert [st for kind, st, _ in acts if kind == oracle.ACT_ADVANCE] == list(range(nt))
+    live, peak = 0, 0
+    steps = 0
+    for kind, st, _ in acts:
+        if kind == oracle.ACT_STORE and st > 0:
+            live += 1
+            peak = max(peak, live)
+        elif kind == oracle.ACT_FREE:
+            live -= 1
+        elif kind in (oracle.ACT_ADVANCE, oracle.ACT_RECOMPUTE):
+            steps += 1
+    assert peak <= s and live == 0
+    assert steps == oracle.binomial_cost(nt, s)
+
+
+@pytest.mark.parametrize("s", [1, 3, 8])
+def test_binomial_raw_bitwise_equals_full_history(oracle, s):
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    g_full, phi_full, d_full, _ = oracle.gradient(g, m, q, src, rec, dobs)
+    g_b, phi_b, d_b, _ = oracle.gradient(g, m, q, src, rec, dobs, mode=oracle.CKPT_BINOMIAL, k=s)
+    assert np.array_equal(g_full, g_b) and phi_full == phi_b and np.array_equal(d_full, d_b)
+
+
+def test_binomial_compressed_close_to_full(oracle):
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    g_ref, phi_ref, *_ = oracle.gradient(g, m, q, src, rec, dobs)
+    gz, phi_z, *_ = oracle.gradient(g, m, q, src, rec, dobs, mode=oracle.CKPT_BINOMIAL, k=3, atol=1e-6)
+    assert phi_z == phi_ref   # data come from the exact first forward pass
+    assert np.linalg.norm(gz - g_ref) / np.linalg.norm(g_ref) < 1e-3
+
+
+def test_subsampling_f1_is_full_history(oracle):
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    g_full, phi, *_ = oracle.gradient(g, m, q, src, rec, dobs)
+    g_s, phi_s, *_ = oracle.gradient(g, m, q, src, rec, dobs, mode=oracle.CKPT_SUBSAMPLE, k=1)
+    assert np.array_equal(g_full, g_s) and phi == phi_s
+
+
+def test_subsampling_error_grows_with_factor(oracle):
+    """Subsampled imaging (Sec. 4.7): the gradient's angle to the full one
+    grows with the subsampling factor while the stored states shrink as 1/f."""
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    g_full, *_ = oracle.gradient(g, m, q, src, rec, dobs)
+    angles = []
+    for f in (2, 4, 8, 16):
+        gs, _, _, nbytes = oracle.gradient(g, m, q, src, rec, dobs, mode=oracle.CKPT_SUBSAMPLE, k=f)
+        cos = np.vdot(gs, g_full) / (np.linalg.norm(gs) * np.linalg.norm(g_full))
+        angles.append(np.arccos(min(1.0, cos)))
+        assert nbytes == (NT // f) * m.size * 4
+    # grows, then saturates near the paper's largest angles (~0.8 rad at f=20)
+    assert angles[0] < angles[1] < angles[2], angles
+    assert min(angles[2:]) > 0.5, angles
+    acts = oracle.ckpt_schedule(NT, oracle.CKPT_SUBSAMPLE, 4)
+    assert sum(1 for k, *_ in acts if k == oracle.ACT_STORE) == NT // 4
