@@ -624,6 +624,7 @@ cudaError_t zfp_encode_launch(const float* in, Grid g, int minexp, uint8_t* out,
                               const unsigned long long* d_base, size_t capacity,
                               unsigned long long* d_size, int* d_status, void* scratch,
                               cudaStream_t s) {
+  if (!scratch) return cudaErrorInvalidValue;
   EncArgs a = encode_args(in, g, minexp, out, d_base, capacity, d_size, d_status);
   const long ntiles = (a.nchunks + kTile - 1) / kTile;
   StageArgs st;
@@ -652,6 +653,7 @@ cudaError_t zfp_encode_chained_launch(const float* in, Grid g, int minexp, uint8
                                       const unsigned long long* d_base, size_t capacity,
                                       unsigned long long* d_size, int* d_status,
                                       unsigned long long* scratch, cudaStream_t s) {
+  if (!scratch) return cudaErrorInvalidValue;
   EncArgs a = encode_args(in, g, minexp, out, d_base, capacity, d_size, d_status);
   cudaError_t e = cudaMemsetAsync(scratch, 0, (size_t)(a.nchunks + 1) * 8, s);
   if (e != cudaSuccess) return e;

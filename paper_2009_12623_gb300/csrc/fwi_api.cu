@@ -621,7 +621,9 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
   unsigned long long* offs = store->d_offs;
   unsigned long long* sizes = store->d_offs + store->slot_cap;
   unsigned long long* d_peak = store->d_offs + 2 * store->slot_cap;  // largest arena end so far
-  void* scratch = lossy && do_fwd ? (void*)pool.get<unsigned char>(zfp_encode_scratch_bytes(G.nx, G.ny, G.nz)) : nullptr;
+  // binomial schedules also store snapshots during the reverse sweep
+  const bool encodes = lossy && (do_fwd || binom);
+  void* scratch = encodes ? (void*)pool.get<unsigned char>(zfp_encode_scratch_bytes(G.nx, G.ny, G.nz)) : nullptr;
   const int K = pol->mode == FWI_CKPT_EVERY_K ? pol->k_or_snaps : 1;
   std::vector<float*> ring(K, nullptr);
   for (int i = 0; i < K; ++i) ring[i] = pool.get<float>(G.cells());
@@ -870,6 +872,9 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
     store->geom = *g;
     store->pol = *pol;
   }
+  // a binomial reverse half reuses the snapshot slots of the forward half,
+  // so the store no longer holds that forward sweep
+  if (binom && do_rev && !do_fwd) store->filled = false;
   if (do_rev) {
     CK(unpack_add_launch(gacc, G, d_grad, s));
     CK(cudaStreamSynchronize(s));
