@@ -177,6 +177,82 @@ int fwi_gradient_host(const fwi_geometry* g, const float* h_m, const float* h_wa
                       const float* h_obs, float* h_grad, double* h_misfit, fwi_ckpt_store* st,
                       const fwi_ckpt_policy* pol, void* stream);
 
+/* ---- batched shots (Sec. 2: the misfit and its gradient are sums over
+ * shots; Sec. 3: every shot images only its own part of the model) -------- */
+/* One shot of a batch.  The shot is modelled on its aperture: the sub-grid
+ * nx*ny*nz at (x0, y0, z0) of the model grid, with the absorbing layer of
+ * fwi_geometry (nbl, sponge_R, vmax) inside the aperture on all six faces, as
+ * if fwi_gradient were called on that window of the model.  Source and
+ * receivers are in model-grid coordinates and must lie in the aperture. */
+typedef struct {
+  int x0, y0, z0;          /* aperture origin in the model grid (cells) */
+  int nx, ny, nz;          /* aperture extent (cells) */
+  int nt;                  /* record length of this shot (steps, >= 1) */
+  int src_i, src_j, src_k; /* source cell */
+  int rec_first, nrec;     /* its receivers: rows rec_first .. rec_first+nrec-1 of d_rec_ijk */
+  long long wavelet_first; /* its nt source samples start at h_wavelets[wavelet_first] */
+  long long obs_first;     /* its nt*nrec samples (time-major) start at d_obs[obs_first]
+                              (likewise in d_rec_out and d_resid) */
+} fwi_shot;
+
+/* A batch plan owns everything the shots need on the device: per-shot
+ * wavefields and model windows, the checkpoint arena (arena_bytes), the
+ * launch configuration and, with FWI_BATCH_GRAPH, the CUDA graph of a whole
+ * call, captured on first use and replayed while the call's device pointers
+ * stay the same.  All shots advance together, one launch per time step
+ * covering the tiles of every active shot; checkpoints follow pol (modes
+ * FWI_CKPT_FULL and FWI_CKPT_EVERY_K) for each shot independently, and the
+ * result of every shot equals that of a single-shot call on its aperture.
+ *   g          model grid (nx, ny, nz), h, dt and absorbing layer; g->nt is unused
+ *   h_shots    nshots shot descriptions (host, copied)
+ *   d_rec_ijk  receiver cells (i,j,k) in model-grid coordinates, int32, used
+ *              during this call only
+ *   flags      FWI_BATCH_GRAPH and/or FWI_BATCH_TUNE (pick the tile depth and
+ *              the persistent grid size by timing candidates on the plan's
+ *              own fields, at the first call)
+ * FWI_ERR_CAPACITY when pol stores raw fields that cannot fit in arena_bytes;
+ * FWI_ERR_NOMEM when the working set does not fit on the device. */
+#define FWI_BATCH_GRAPH 1
+#define FWI_BATCH_TUNE 2
+typedef struct fwi_batch fwi_batch;
+int fwi_batch_create(const fwi_geometry* g, int nshots, const fwi_shot* h_shots, const int* d_rec_ijk,
+                     const fwi_ckpt_policy* pol, size_t arena_bytes, int flags, fwi_batch** out);
+int fwi_batch_destroy(fwi_batch* b);
+
+/* Stacked gradient of all shots: d_grad (model grid) += sum over shots of
+ * the shot's dPhi_s/dm placed at its aperture, in shot order;
+ * h_misfit[s] = Phi_s (FP64).  d_m is the model (model grid), h_wavelets the
+ * source samples, d_obs the observed records.  Synchronises.
+ * FWI_ERR_CAPACITY if the compressed checkpoints overflow the arena. */
+int fwi_batch_gradient(fwi_batch* b, const float* d_m, const float* h_wavelets, const float* d_obs,
+                       float* d_grad, double* h_misfit, void* stream);
+/* The two halves, as fwi_forward_store / fwi_adjoint_store for each shot:
+ * the forward records (d_rec_out, laid out like d_obs) with the checkpoints
+ * kept in the plan, then d_grad += sum_s J_s^T d_resid_s.  The adjoint call
+ * needs a completed forward call on the same plan (FWI_ERR_ARG otherwise). */
+int fwi_batch_forward(fwi_batch* b, const float* d_m, const float* h_wavelets, float* d_rec_out,
+                      void* stream);
+int fwi_batch_adjoint(fwi_batch* b, const float* d_m, const float* h_wavelets, const float* d_resid,
+                      float* d_grad, void* stream);
+
+/* Configuration and counters of a plan. */
+typedef struct {
+  int nshots;
+  int max_nt;             /* longest record (steps) */
+  int zc;                 /* tile depth (z planes per tile) of the forward kernel, 0 = per-shot automatic */
+  int ctas;               /* CTAs of each persistent forward-stencil launch */
+  int zc_adjoint;         /* the same for the adjoint kernel */
+  int ctas_adjoint;
+  int tuned;              /* 1 once the autotuner has run */
+  int graph_nodes;        /* nodes of the last captured graph (0: none) */
+  uint64_t launches_per_call; /* kernels one gradient call launches */
+  size_t arena_bytes;
+  size_t used_bytes;      /* checkpoint bytes of the last forward sweep */
+  size_t raw_bytes;       /* the same checkpoints uncompressed */
+  size_t device_bytes;    /* device memory the plan holds */
+} fwi_batch_stats;
+int fwi_batch_get_stats(const fwi_batch* b, fwi_batch_stats* out);
+
 /* ---- fixed-accuracy codec (Sec. 1.3) -------------------------------------- */
 /* Stream format (shared bit-for-bit with the CPU oracle):
  *   64-byte header (magic "FCZ1", version, nx, ny, nz, minexp, nblocks,

@@ -94,6 +94,8 @@ def lib():
             L.oracle_zfp_block_quantise.argtypes = [fp, C.c_int, C.POINTER(C.c_int32), ip, ip]
             L.oracle_num_threads.restype = C.c_int
             L.oracle_binomial_cost.argtypes = [C.c_int, C.c_int]
+            L.oracle_gradient_batch.argtypes = [gp, dp, C.c_int, C.POINTER(Shot), dp, ip, dp,
+                                                C.POINTER(Policy), dp, dp]
             L.oracle_binomial_cost.restype = C.c_longlong
             _lib = L
     return _lib
@@ -184,6 +186,43 @@ def gradient(g, m, wavelet, src, rec, d_obs, mode=CKPT_FULL, k=1, atol=0.0, m0=N
     if st:
         raise RuntimeError(f"oracle_gradient failed: {st}")
     return grad, phi.value, dsim, nbytes.value
+
+
+class Shot(C.Structure):
+    _fields_ = [("x0", C.c_int), ("y0", C.c_int), ("z0", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+                ("nz", C.c_int), ("nt", C.c_int), ("src_i", C.c_int), ("src_j", C.c_int),
+                ("src_k", C.c_int), ("rec_first", C.c_int), ("nrec", C.c_int),
+                ("wavelet_first", C.c_longlong), ("obs_first", C.c_longlong)]
+
+
+def gradient_batch(g, m, shots, wavelets, recs, d_obs, mode=CKPT_FULL, k=1, atol=0.0):
+    """Stacked gradient of a survey.  shots: sequence of (x0, y0, z0, nx, ny,
+    nz, nt, (si, sj, sk)) in model-grid cells; wavelets[s]: (nt,) samples;
+    recs[s]: (nrec, 3) receiver cells (model grid); d_obs[s]: (nt, nrec).
+    Returns (grad on the model grid, misfit per shot), FP64."""
+    g = _geom(g)
+    m = _f64(m)
+    arr = (Shot * max(len(shots), 1))()
+    wf = of = rf = 0
+    for i, (x0, y0, z0, nx, ny, nz, nt, src) in enumerate(shots):
+        nrec = len(recs[i])
+        arr[i] = Shot(x0, y0, z0, nx, ny, nz, nt, int(src[0]), int(src[1]), int(src[2]), rf, nrec, wf, of)
+        wf += nt
+        of += nt * nrec
+        rf += nrec
+    w = _f64(np.concatenate([np.asarray(x, np.float64).ravel() for x in wavelets]) if shots else np.zeros(1))
+    rr = np.ascontiguousarray(np.concatenate([np.asarray(r, np.int32).reshape(-1, 3) for r in recs])
+                              if rf else np.zeros((1, 3)), dtype=np.int32)
+    dob = _f64(np.concatenate([np.asarray(d, np.float64).ravel() for d in d_obs]) if of else np.zeros(1))
+    grad = np.zeros_like(m)
+    phi = np.zeros(max(len(shots), 1))
+    pol = Policy(mode, k, atol)
+    st = lib().oracle_gradient_batch(C.byref(g), _p(m, C.c_double), len(shots), arr, _p(w, C.c_double),
+                                     _p(rr, C.c_int), _p(dob, C.c_double), C.byref(pol),
+                                     _p(grad, C.c_double), _p(phi, C.c_double))
+    if st:
+        raise RuntimeError(f"oracle_gradient_batch failed: {st}")
+    return grad, phi[: len(shots)]
 
 
 def binomial_cost(n, s):

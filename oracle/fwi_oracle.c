@@ -514,3 +514,54 @@ int oracle_gradient(const oracle_geometry* g, const double* m, const double* m0,
   free(dsim); free(resid); free(lnext); free(lcur); free(lnew);
   return st;
 }
+
+int oracle_gradient_batch(const oracle_geometry* g, const double* m, int nshots,
+                          const oracle_shot* shots, const double* wavelets,
+                          const int* rec_ijk, const double* d_obs,
+                          const oracle_policy* pol, double* grad, double* misfit) {
+  if (oc_check(g) || !m || nshots < 0 || (nshots > 0 && (!shots || !wavelets)) || !pol || !grad ||
+      !misfit)
+    return ORACLE_ERR_ARG;
+  for (int s = 0; s < nshots; s++) {
+    const oracle_shot* sh = &shots[s];
+    if (sh->nx < 1 || sh->ny < 1 || sh->nz < 1 || sh->x0 < 0 || sh->y0 < 0 || sh->z0 < 0 ||
+        sh->x0 + sh->nx > g->nx || sh->y0 + sh->ny > g->ny || sh->z0 + sh->nz > g->nz ||
+        sh->nt < 0 || sh->nrec < 0 || (sh->nrec > 0 && (!rec_ijk || !d_obs)))
+      return ORACLE_ERR_ARG;
+    /* the shot's own problem: its window of the model and local coordinates */
+    oracle_geometry lg = *g;
+    lg.nx = sh->nx;
+    lg.ny = sh->ny;
+    lg.nz = sh->nz;
+    lg.nt = sh->nt;
+    long C = (long)sh->nx * sh->ny * sh->nz;
+    double* mw = (double*)malloc(sizeof(double) * C);
+    double* gw = (double*)calloc(C, sizeof(double));
+    int* rl = (int*)malloc(sizeof(int) * 3 * (sh->nrec > 0 ? sh->nrec : 1));
+    for (int k = 0; k < sh->nz; k++)
+      for (int j = 0; j < sh->ny; j++)
+        for (int i = 0; i < sh->nx; i++)
+          mw[i + (long)sh->nx * (j + (long)sh->ny * k)] =
+              m[(sh->x0 + i) + (long)g->nx * ((sh->y0 + j) + (long)g->ny * (sh->z0 + k))];
+    const int* rg = rec_ijk ? rec_ijk + 3L * sh->rec_first : NULL;
+    for (int r = 0; r < sh->nrec; r++) {
+      rl[3 * r] = rg[3 * r] - sh->x0;
+      rl[3 * r + 1] = rg[3 * r + 1] - sh->y0;
+      rl[3 * r + 2] = rg[3 * r + 2] - sh->z0;
+    }
+    int st = oracle_gradient(&lg, mw, NULL, wavelets + sh->wavelet_first, sh->src_i - sh->x0,
+                             sh->src_j - sh->y0, sh->src_k - sh->z0, rl, sh->nrec,
+                             d_obs ? d_obs + sh->obs_first : NULL, pol, gw, &misfit[s], NULL, NULL);
+    if (!st)
+      for (int k = 0; k < sh->nz; k++)
+        for (int j = 0; j < sh->ny; j++)
+          for (int i = 0; i < sh->nx; i++)
+            grad[(sh->x0 + i) + (long)g->nx * ((sh->y0 + j) + (long)g->ny * (sh->z0 + k))] +=
+                gw[i + (long)sh->nx * (j + (long)sh->ny * k)];
+    free(mw);
+    free(gw);
+    free(rl);
+    if (st) return st;
+  }
+  return ORACLE_OK;
+}

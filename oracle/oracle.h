@@ -128,6 +128,33 @@ int oracle_gradient(const oracle_geometry* g, const double* m, const double* m0,
                     const oracle_policy* pol, double* grad, double* misfit,
                     double* d_sim_out, double* ckpt_bytes_out);
 
+/* One shot of a survey, modelled on its aperture: the nx*ny*nz window at
+ * (x0, y0, z0) of the model grid, with the absorbing layer inside the
+ * window.  Source and receivers are in model-grid coordinates; the shot's
+ * nt source samples start at wavelets[wavelet_first], its nt*nrec observed
+ * samples (time-major) at d_obs[obs_first], its receivers at row rec_first
+ * of rec_ijk. */
+typedef struct {
+  int x0, y0, z0, nx, ny, nz;
+  int nt;
+  int src_i, src_j, src_k;
+  int rec_first, nrec;
+  long long wavelet_first, obs_first;
+} oracle_shot;
+
+/* Stacked gradient of a survey (Sec. 2: Phi = sum over shots of Eq. (3), so
+ * its gradient is the sum of the shots' Eq. (4)): for every shot, the
+ * gradient of oracle_gradient on the shot's window of m (damping weighted
+ * by that window) is added into grad (the model grid) at the window, in shot
+ * order; misfit[s] = Phi_s.  Pinned: one full-grid shot equals
+ * oracle_gradient; translating a shot in a homogeneous model translates its
+ * gradient; a finite-difference derivative of sum_s Phi_s on windows cut by
+ * the test itself; shot order changes nothing beyond rounding. */
+int oracle_gradient_batch(const oracle_geometry* g, const double* m, int nshots,
+                          const oracle_shot* shots, const double* wavelets,
+                          const int* rec_ijk, const double* d_obs,
+                          const oracle_policy* pol, double* grad, double* misfit);
+
 /* Checkpoint schedule for the policy: the ordered list of actions that
  * oracle_gradient executes.  Binomial: with the state at a stored and s more
  * snapshot slots, serving adjoint steps a+n .. a+1 costs

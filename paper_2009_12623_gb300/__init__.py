@@ -12,6 +12,7 @@ from .api import (  # noqa: F401
     FWI_CKPT_EVERY_K,
     FWI_CKPT_FULL,
     FWI_CKPT_SUBSAMPLE,
+    Batch,
     CheckpointStore,
     FwiError,
     Geometry,
@@ -20,8 +21,10 @@ from .api import (  # noqa: F401
     forward,
     gradient,
     gradient_host,
+    gradient_per_shot,
     kernel_launch_count,
     misfit,
+    ShotSpec,
     zfp_compress,
     zfp_decompress,
     zfp_max_compressed_bytes,

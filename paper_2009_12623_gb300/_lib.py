@@ -25,7 +25,8 @@ EXPORTS = [
     "zfp_compress_fixed_accuracy", "zfp_decompress", "fwi_misfit", "fwi_dot_f64",
     "fwi_status_string", "fwi_kernel_launch_count", "fwi_profile_enable", "fwi_profile_reset",
     "fwi_profile_read", "zfp_compress_fixed_accuracy_noalloc", "fwi_forward_store",
-    "fwi_adjoint_store",
+    "fwi_adjoint_store", "fwi_batch_create", "fwi_batch_destroy", "fwi_batch_gradient",
+    "fwi_batch_forward", "fwi_batch_adjoint", "fwi_batch_get_stats",
 ]
 KERNEL_CLASSES = ["stencil_forward", "stencil_adjoint_imaging", "zfp_encode", "zfp_decode", "other"]
 
@@ -54,6 +55,23 @@ class StoreStats(C.Structure):
     _fields_ = [("capacity_bytes", C.c_size_t), ("used_bytes", C.c_size_t),
                 ("raw_bytes", C.c_size_t), ("n_checkpoints", C.c_int), ("overflowed", C.c_int)]
 
+
+class Shot(C.Structure):
+    _fields_ = [("x0", C.c_int), ("y0", C.c_int), ("z0", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+                ("nz", C.c_int), ("nt", C.c_int), ("src_i", C.c_int), ("src_j", C.c_int),
+                ("src_k", C.c_int), ("rec_first", C.c_int), ("nrec", C.c_int),
+                ("wavelet_first", C.c_longlong), ("obs_first", C.c_longlong)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("nshots", C.c_int), ("max_nt", C.c_int), ("zc", C.c_int), ("ctas", C.c_int),
+                ("zc_adjoint", C.c_int), ("ctas_adjoint", C.c_int), ("tuned", C.c_int),
+                ("graph_nodes", C.c_int), ("launches_per_call", C.c_uint64), ("arena_bytes", C.c_size_t),
+                ("used_bytes", C.c_size_t), ("raw_bytes", C.c_size_t), ("device_bytes", C.c_size_t)]
+
+
+FWI_BATCH_GRAPH = 1
+FWI_BATCH_TUNE = 2
 
 _lock = threading.Lock()
 _lib = None
@@ -97,6 +115,13 @@ def load() -> C.CDLL:
         L.fwi_profile_enable.argtypes = [C.c_int]
         L.fwi_profile_reset.argtypes = []
         L.fwi_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.c_int]
+        L.fwi_batch_create.argtypes = [gp, C.c_int, C.POINTER(Shot), ip, pp, C.c_size_t, C.c_int,
+                                       C.POINTER(C.c_void_p)]
+        L.fwi_batch_destroy.argtypes = [vp]
+        L.fwi_batch_gradient.argtypes = [vp, fp, vp, fp, fp, dp, vp]
+        L.fwi_batch_forward.argtypes = [vp, fp, vp, fp, vp]
+        L.fwi_batch_adjoint.argtypes = [vp, fp, vp, fp, fp, vp]
+        L.fwi_batch_get_stats.argtypes = [vp, C.POINTER(BatchStats)]
         _lib = L
         return L
 

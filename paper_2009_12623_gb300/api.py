@@ -293,3 +293,173 @@ def dot_f64(a: torch.Tensor, b: torch.Tensor) -> float:
     check("fwi_dot_f64", _lib.load().fwi_dot_f64(_dev(a, torch.float32, "a"), _dev(b, torch.float32, "b"),
                                                  a.numel(), C.byref(out), _stream()))
     return out.value
+
+
+# ---- batched shots ------------------------------------------------------------
+
+@dataclass
+class ShotSpec:
+    """One shot of a survey on its aperture: the nx*ny*nz window at (x0, y0, z0)
+    of the model grid (absorbing layer inside the window), record length nt
+    steps, source cell `src` and receiver cells `rec` ((nrec, 3) int32, i j k)
+    in model-grid coordinates."""
+    x0: int
+    y0: int
+    z0: int
+    nx: int
+    ny: int
+    nz: int
+    nt: int
+    src: tuple
+    rec: np.ndarray
+
+    @property
+    def window(self):
+        return (slice(self.z0, self.z0 + self.nz), slice(self.y0, self.y0 + self.ny),
+                slice(self.x0, self.x0 + self.nx))
+
+    def local_geometry(self, geom: Geometry) -> Geometry:
+        return Geometry(nx=self.nx, ny=self.ny, nz=self.nz, h=geom.h, dt=geom.dt, nt=self.nt, nbl=geom.nbl,
+                        vmax=geom.vmax, sponge_R=geom.sponge_R)
+
+
+def _concat_host(parts) -> np.ndarray:
+    return np.ascontiguousarray(np.concatenate([_host_f32(p).ravel() for p in parts]), dtype=np.float32)
+
+
+class Batch:
+    """fwi_batch plan: all shots of a survey advanced together (one persistent
+    stencil launch per time step over the tiles of every active shot).
+    `graph` captures a whole call as a CUDA graph replayed on later calls
+    with the same tensors; `tune` times launch shapes on the first call.
+    Records, observed data and residuals are flat float32 tensors with each
+    shot's (nt, nrec) block at `offsets[s]` (see `split`)."""
+
+    def __init__(self, geom: Geometry, shots: list, mode: int = FWI_CKPT_EVERY_K, k: int = 10,
+                 atol: float = 0.0, arena_bytes: int = 1 << 30, graph: bool = False, tune: bool = False,
+                 device=None):
+        self.geom, self.shots = geom, list(shots)
+        self.mode, self.k, self.atol = mode, k, atol
+        n = len(self.shots)
+        arr = (_lib.Shot * max(n, 1))()
+        wf = of = rf = 0
+        self.offsets, self.wavelet_offsets = [], []
+        for i, s in enumerate(self.shots):
+            nrec = int(len(s.rec))
+            arr[i] = _lib.Shot(s.x0, s.y0, s.z0, s.nx, s.ny, s.nz, s.nt, int(s.src[0]), int(s.src[1]),
+                               int(s.src[2]), rf, nrec, wf, of)
+            self.offsets.append(of)
+            self.wavelet_offsets.append(wf)
+            wf += s.nt
+            of += s.nt * nrec
+            rf += nrec
+        self.n_obs, self.n_wavelet = of, wf
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        recs = [np.asarray(s.rec, np.int32).reshape(-1, 3) for s in self.shots]
+        rec = torch.from_numpy(np.ascontiguousarray(np.concatenate(recs) if rf else np.zeros((1, 3), np.int32)))
+        self.rec = rec.to(dev)
+        self.device = dev
+        pol = _lib.Policy(mode, k, atol)
+        flags = (_lib.FWI_BATCH_GRAPH if graph else 0) | (_lib.FWI_BATCH_TUNE if tune else 0)
+        h = C.c_void_p()
+        g = geom.cstruct()
+        torch.cuda.synchronize(dev)
+        check("fwi_batch_create", _lib.load().fwi_batch_create(C.byref(g), n, arr, self.rec.data_ptr(),
+                                                                C.byref(pol), arena_bytes, flags, C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("batch plan is closed")
+        return self._h
+
+    def split(self, flat: torch.Tensor) -> list:
+        """Per-shot (nt, nrec) views of a flat records / data tensor."""
+        return [flat[o:o + s.nt * len(s.rec)].view(s.nt, len(s.rec)) for o, s in zip(self.offsets, self.shots)]
+
+    def concat(self, parts) -> torch.Tensor:
+        """Flat device tensor from per-shot (nt, nrec) blocks."""
+        return torch.cat([torch.as_tensor(p, dtype=torch.float32).reshape(-1) for p in parts]).to(self.device)
+
+    def _wavelets(self, wavelets) -> np.ndarray:
+        w = _concat_host(wavelets) if isinstance(wavelets, (list, tuple)) else _host_f32(wavelets).ravel()
+        if w.size < self.n_wavelet:
+            raise ValueError("wavelets shorter than the shots' record lengths")
+        return np.ascontiguousarray(w)
+
+    def gradient(self, m: torch.Tensor, wavelets, d_obs: torch.Tensor, grad: torch.Tensor | None = None):
+        """fwi_batch_gradient: (grad += sum_s dPhi_s/dm, misfits (nshots,) FP64)."""
+        w = self._wavelets(wavelets)
+        if grad is None:
+            grad = torch.zeros(self.geom.shape, dtype=torch.float32, device=m.device)
+        phi = (C.c_double * max(len(self.shots), 1))()
+        st = _lib.load().fwi_batch_gradient(self.handle, _dev(m, torch.float32, "m"), w.ctypes.data,
+                                            _dev(d_obs, torch.float32, "d_obs"), _dev(grad, torch.float32, "grad"),
+                                            phi, _stream())
+        check("fwi_batch_gradient", st)
+        return grad, np.array(phi[: len(self.shots)])
+
+    def forward(self, m: torch.Tensor, wavelets, out: torch.Tensor | None = None) -> torch.Tensor:
+        """fwi_batch_forward: flat records of all shots; checkpoints kept in the plan."""
+        w = self._wavelets(wavelets)
+        if out is None:
+            out = torch.empty(max(self.n_obs, 1), dtype=torch.float32, device=m.device)
+        st = _lib.load().fwi_batch_forward(self.handle, _dev(m, torch.float32, "m"), w.ctypes.data,
+                                           _dev(out, torch.float32, "d"), _stream())
+        check("fwi_batch_forward", st)
+        return out[: self.n_obs]
+
+    def adjoint(self, m: torch.Tensor, wavelets, resid: torch.Tensor, grad: torch.Tensor | None = None):
+        """fwi_batch_adjoint: grad += sum_s J_s^T resid_s from the plan's checkpoints."""
+        w = self._wavelets(wavelets)
+        if grad is None:
+            grad = torch.zeros(self.geom.shape, dtype=torch.float32, device=m.device)
+        st = _lib.load().fwi_batch_adjoint(self.handle, _dev(m, torch.float32, "m"), w.ctypes.data,
+                                           _dev(resid, torch.float32, "resid"), _dev(grad, torch.float32, "grad"),
+                                           _stream())
+        check("fwi_batch_adjoint", st)
+        return grad
+
+    def stats(self) -> dict:
+        s = _lib.BatchStats()
+        check("fwi_batch_get_stats", _lib.load().fwi_batch_get_stats(self.handle, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in _lib.BatchStats._fields_}
+
+    def close(self):
+        if self._h:
+            _lib.load().fwi_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gradient_per_shot(geom: Geometry, m: torch.Tensor, shots: list, wavelets, d_obs: list,
+                      store: CheckpointStore, mode: int = FWI_CKPT_FULL, k: int = 1, atol: float = 0.0,
+                      grad: torch.Tensor | None = None):
+    """One fwi_gradient call per shot on its window of the model (the plain,
+    one-shot-per-launch-sequence path): returns (grad += sum_s dPhi_s/dm,
+    misfits).  The window copy of m and the stacking add are tensor copies."""
+    if grad is None:
+        grad = torch.zeros(geom.shape, dtype=torch.float32, device=m.device)
+    phis = []
+    for i, s in enumerate(shots):
+        lg = s.local_geometry(geom)
+        mw = m[s.window].contiguous()
+        origin = torch.tensor([s.x0, s.y0, s.z0], dtype=torch.int32, device=m.device)
+        rec = (torch.as_tensor(np.asarray(s.rec, np.int32), device=m.device) - origin).contiguous()
+        src = (s.src[0] - s.x0, s.src[1] - s.y0, s.src[2] - s.z0)
+        g, phi = gradient(lg, mw, wavelets[i], src, rec, d_obs[i], store, mode=mode, k=k, atol=atol)
+        grad[s.window] += g
+        phis.append(phi)
+    return grad, np.array(phis)

@@ -12,6 +12,8 @@ namespace fwi {
 
 // ---- launch accounting and optional per-kernel timing ------------------------
 void count_launch();
+void count_launches(unsigned long long n);  // kernels of a replayed CUDA graph
+unsigned long long launches_so_far();
 // Kernel classes timed by fwi_profile_* (CUDA events on the launching stream).
 enum KernelClass : int {
   KC_STENCIL_FWD = 0,
@@ -120,18 +122,66 @@ cudaError_t rec_fac_launch(const StencilParams& p, const long* rec_cell, int nre
 // d_row[r] = field[rec_cell[r]]
 cudaError_t gather_launch(const float* field, const long* rec_cell, int nrec, float* d_row,
                           cudaStream_t s);
-// rec_cell[r] = pitched cell of (i,j,k); flags ST_CORRUPT (as "bad index") on out-of-range.
+// rec_cell[r] = pitched cell of (i,j,k) - (ox,oy,oz); flags ST_CORRUPT (as
+// "bad index") when that lies outside the grid.
 cudaError_t rec_cells_launch(const int* rec_ijk, int nrec, Grid g, long* rec_cell, int* d_status,
-                             cudaStream_t s);
-// Setup: b = dt^2/m (pitched, zero in padding), damping profiles.
+                             cudaStream_t s, int ox = 0, int oy = 0, int oz = 0);
+// Setup: b = dt^2/m (pitched, zero in padding), damping profiles.  The model
+// may be a larger packed array (rows of mnx, mny rows per plane; 0 = the
+// grid's own) of which the window at (ox, oy, oz) is used.
 cudaError_t setup_model_launch(const float* m, Grid g, float dt, float* b, int* d_status,
-                               cudaStream_t s);
+                               cudaStream_t s, int mnx = 0, int mny = 0, int ox = 0, int oy = 0,
+                               int oz = 0);
 cudaError_t setup_profiles_launch(Grid g, int nbl, double h, double vmax, double R, double dt,
                                   float* sx, float* sy, float* sz, cudaStream_t s);
 // Pitched <-> packed copies.
 cudaError_t pack_launch(const float* pitched, Grid g, float* packed, cudaStream_t s);
 cudaError_t unpack_launch(const float* packed, Grid g, float* pitched, cudaStream_t s);
 cudaError_t unpack_add_launch(const float* pitched, Grid g, float* packed, cudaStream_t s);
+// dst (packed, gnx x gny per plane) at window (ox, oy, oz) += pitched field.
+cudaError_t stack_add_launch(const float* pitched, Grid g, float* dst, int gnx, int gny, int ox, int oy,
+                             int oz, cudaStream_t s);
+
+// ---- many fields per launch (batched shots) ---------------------------------
+constexpr int kStencilMaxFields = 32;
+// One field of a multi-field stencil launch: the step (forward, with its
+// point source) or the adjoint step with imaging, as in the single-field calls.
+struct StencilField {
+  const float* cur;
+  const float* prev;
+  float* out;
+  long src_cell;          // forward: injection cell or -1
+  const float* wavelet;   // forward: source samples (device)
+  int n;                  // forward: time index of the sample
+  const float* uk;        // adjoint: forward state for the imaging condition
+  float* grad;            // adjoint: gradient accumulator
+  int zc;                 // z-chunk of the tiles (0: automatic)
+};
+// Resident CTAs of the multi-field kernel on the whole GPU (0 on failure).
+int stencil_multi_capacity();
+// One persistent launch over the tiles of all fields; ctas <= 0 = resident capacity.
+cudaError_t stencil_multi_launch(bool adjoint, int nfields, const StencilParams* const* p,
+                                 const StencilField* f, float weight, int ctas, cudaStream_t s);
+struct RecTask {
+  const float* field;   // gather: sampled field
+  float* row_out;       // gather: output row
+  const long* cell;
+  const float* fac;     // inject: weights
+  const float* row_in;  // inject: residual row
+  float* out;           // inject: adjoint field
+  const float* uk;      // inject: forward state (NULL: no imaging term)
+  float* grad;
+};
+struct MultiRec {
+  RecTask t[kStencilMaxFields];
+  int first[kStencilMaxFields + 1];
+  int nfields;
+  float idt2;
+};
+cudaError_t gather_multi_launch(int nfields, const RecTask* t, const int* nrec, cudaStream_t s);
+cudaError_t inject_multi_launch(int nfields, const RecTask* t, const int* nrec, float dt, float weight,
+                                cudaStream_t s);
+
 // Residual r = a - b, FP64 half-sum-of-squares added to *d_acc; dot product
 // likewise.  `part` holds reduce_scratch_doubles() doubles; the summation
 // order is fixed, so results are bitwise reproducible.

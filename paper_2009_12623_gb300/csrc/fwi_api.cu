@@ -16,11 +16,14 @@
 #include <vector>
 
 #include "common.cuh"
+#include "runtime.cuh"
 
 namespace fwi {
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---- per-kernel timing: event pairs recorded around launches ---------------
 namespace {
@@ -73,6 +76,11 @@ void prof_drain(bool wait) {
 int prof_begin(int cls, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return -1;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return -1;  // launches inside a CUDA graph are not timed one by one
+  }
   if (g_prof_slots.size() > 4096) prof_drain(false);
   cudaEvent_t a = prof_event(), b = prof_event();
   if (!a || !b) return -1;
@@ -96,96 +104,6 @@ int status_from_flags(int f) {
 }
 
 namespace {
-
-// 8th-order central second-difference weights (times h^2).
-const double kC[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
-
-// Stream-ordered allocations released when the scope ends.
-struct Pool {
-  cudaStream_t s;
-  std::vector<void*> ptrs;
-  bool failed = false;
-  explicit Pool(cudaStream_t st) : s(st) {}
-  template <class T>
-  T* get(size_t n) {
-    void* p = nullptr;
-    if (n == 0) n = 1;
-    if (cudaMallocAsync(&p, n * sizeof(T), s) != cudaSuccess) {
-      failed = true;
-      cudaGetLastError();
-      return nullptr;
-    }
-    ptrs.push_back(p);
-    return static_cast<T*>(p);
-  }
-  ~Pool() {
-    for (void* p : ptrs) cudaFreeAsync(p, s);
-  }
-};
-
-// A second stream for codec work with a few events; on destruction the
-// owner's stream waits for everything issued on it (so stream-ordered frees
-// on the owner's stream stay safe on every return path).
-struct CodecStream {
-  cudaStream_t owner;
-  cudaStream_t s = nullptr;
-  cudaEvent_t ev[8] = {nullptr};
-  cudaEvent_t done = nullptr;
-  bool ok = false;
-  explicit CodecStream(cudaStream_t o) : owner(o) {
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-      cudaGetLastError();
-      return;
-    }
-    for (auto& e : ev)
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-      }
-    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      return;
-    }
-    // codec work may only start after everything the owner issued so far
-    ok = cudaEventRecord(done, owner) == cudaSuccess && cudaStreamWaitEvent(s, done, 0) == cudaSuccess;
-  }
-  // owner waits for all codec work issued so far
-  cudaError_t join() {
-    cudaError_t e = cudaEventRecord(done, s);
-    if (e != cudaSuccess) return e;
-    return cudaStreamWaitEvent(owner, done, 0);
-  }
-  ~CodecStream() {
-    if (s) {
-      join();
-      cudaStreamDestroy(s);
-    }
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
-    if (done) cudaEventDestroy(done);
-    cudaGetLastError();
-  }
-};
-
-bool geometry_ok(const fwi_geometry* g) {
-  return g && g->nx > 0 && g->ny > 0 && g->nz > 0 && g->nt >= 0 && g->h > 0 && g->dt > 0 &&
-         g->nbl >= 0 && (g->nbl == 0 || (g->sponge_R > 0 && g->sponge_R < 1 && g->vmax > 0)) &&
-         (long)g->nx * g->ny * g->nz < (1L << 40);
-}
-
-int minexp_of(double atol) {
-  int e;
-  frexp(atol, &e);
-  return e - 1;
-}
-
-#define CK(x)                          \
-  do {                                 \
-    if ((x) != cudaSuccess) {          \
-      cudaGetLastError();              \
-      return FWI_ERR_CUDA;             \
-    }                                  \
-  } while (0)
 
 // Everything the sweeps need on the device.
 struct Sweep {
@@ -375,9 +293,8 @@ int make_schedule(int nt, const fwi_ckpt_policy* pol, Sched& out) {
   return FWI_ERR_ARG;
 }
 
-// Offset bookkeeping for compressed slots: the next slot starts where the
-// previous one ended (256-byte aligned).  Runs on the device so that no host
-// synchronisation is needed between checkpoints.
+}  // namespace
+
 __global__ void k_slot_offset(unsigned long long* off, const unsigned long long* size, int j) {
   off[j] = j == 0 ? 0ull : off[j - 1] + ((size[j - 1] + 255ull) & ~255ull);
 }
@@ -386,26 +303,23 @@ __global__ void k_track_peak(const unsigned long long* off, const unsigned long 
   const unsigned long long e = off[j] + ((size[j] + 255ull) & ~255ull);
   if (e > *peak) *peak = e;
 }
+cudaError_t slot_offset_launch(unsigned long long* off, const unsigned long long* size, int j,
+                               cudaStream_t s) {
+  k_slot_offset<<<1, 1, 0, s>>>(off, size, j);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t track_peak_launch(const unsigned long long* off, const unsigned long long* size, int j,
+                              unsigned long long* peak, cudaStream_t s) {
+  k_track_peak<<<1, 1, 0, s>>>(off, size, j, peak);
+  count_launch();
+  return cudaGetLastError();
+}
 
-}  // namespace
 }  // namespace fwi
 
 using namespace fwi;
 
-struct fwi_ckpt_store {
-  uint8_t* arena = nullptr;
-  size_t capacity = 0;
-  fwi_store_stats stats{};
-  // slot table of the last forward sweep (device), kept for a later reverse sweep
-  unsigned long long* d_offs = nullptr;
-  unsigned long long* d_sizes = nullptr;
-  int slot_cap = 0;
-  bool filled = false;  // a forward sweep completed and its checkpoints are in the arena
-  float* carry = nullptr;  // binomial: final forward state pair kept between the two halves
-  size_t carry_bytes = 0;
-  fwi_geometry geom{};
-  fwi_ckpt_policy pol{};
-};
 
 extern "C" {
 
@@ -643,14 +557,10 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
   if (!cs.ok) return FWI_ERR_CUDA;
   auto store_field = [&](const float* f, int j) -> int {
     if (lossy) {
-      k_slot_offset<<<1, 1, 0, cs.s>>>(offs, sizes, j);
-      count_launch();
-      CK(cudaGetLastError());
+      CK(slot_offset_launch(offs, sizes, j, cs.s));
       CK(zfp_encode_launch(f, G, minexp, store->arena, offs + j, store->capacity, sizes + j,
                            sw.d_status, scratch, cs.s));
-      k_track_peak<<<1, 1, 0, cs.s>>>(offs, sizes, j, d_peak);
-      count_launch();
-      CK(cudaGetLastError());
+      CK(track_peak_launch(offs, sizes, j, d_peak, cs.s));
     } else {
       CK(cudaMemcpyAsync(store->arena + (size_t)j * raw_slot, f, fbytes, cudaMemcpyDeviceToDevice, cs.s));
     }

@@ -17,7 +17,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .api import Geometry
+from .api import Geometry, ShotSpec
 
 
 def ricker(t, f: float, t0: float):
@@ -183,3 +183,49 @@ def shells_field(n: int = 512, seed: int = 0, nshell: int = 8, f: float = 15.0, 
         out[z0:z1] = acc
     out += (noise * rng.normal(size=out.shape)).astype(np.float32)
     return out
+
+
+@dataclass
+class Survey:
+    """Many shots over one model: `geom` is the model grid (nt = the longest
+    record), each ShotSpec gives a shot's aperture, record length, source
+    and receivers."""
+    geom: Geometry
+    f: float
+    v_true: np.ndarray
+    v0: np.ndarray
+    shots: list
+
+    def wavelets(self) -> list:
+        return [wavelet(s.nt, self.geom.dt, self.f) for s in self.shots]
+
+
+def batch_survey(nx: int = 600, ny: int = 600, nz: int = 200, nshots: int = 32, h: float = 20.0,
+                 dt: float = 1.5e-3, f: float = 10.0, nbl: int = 40, ap_min: int = 200, ap_max: int = 600,
+                 t_min: float = 1.5, t_max: float = 3.0, rec_stride: int = 4, seed: int = 0,
+                 vmin: float = 1500.0, vmax: float = 6000.0, smooth_cells: float = 6.0) -> Survey:
+    """Batched-shot survey over the layered model: per shot, aperture sides
+    (x, y) uniform in [ap_min, ap_max] cells (full depth), centred on a source
+    drawn uniformly over the surface at depth nbl+2 and shifted to stay in the
+    grid, record length uniform in [t_min, t_max] s, receivers on every
+    rec_stride-th (x, y) node of the aperture at the source depth."""
+    rng = np.random.default_rng(seed)
+    v_true = layered_velocity(nx, ny, nz, seed=seed, water=min(nbl + 10, nz // 3), vmin=vmin, vmax=vmax)
+    v0 = smooth(v_true, smooth_cells)
+    zs = min(nbl + 2, nz - 1)
+    shots = []
+    for _ in range(nshots):
+        ax = min(int(rng.integers(ap_min, ap_max + 1)), nx)
+        ay = min(int(rng.integers(ap_min, ap_max + 1)), ny)
+        sx, sy = int(rng.integers(0, nx)), int(rng.integers(0, ny))
+        x0 = int(np.clip(sx - ax // 2, 0, nx - ax))
+        y0 = int(np.clip(sy - ay // 2, 0, ny - ay))
+        sx = int(np.clip(sx, x0, x0 + ax - 1))
+        sy = int(np.clip(sy, y0, y0 + ay - 1))
+        nt = max(1, int(round(rng.uniform(t_min, t_max) / dt)))
+        X, Y = np.meshgrid(np.arange(x0, x0 + ax, rec_stride), np.arange(y0, y0 + ay, rec_stride), indexing="xy")
+        rec = np.stack([X.ravel(), Y.ravel(), np.full(X.size, zs)], axis=1).astype(np.int32)
+        shots.append(ShotSpec(x0, y0, 0, ax, ay, nz, nt, (sx, sy, zs), rec))
+    geom = Geometry(nx=nx, ny=ny, nz=nz, h=h, dt=dt, nt=max(s.nt for s in shots), nbl=nbl,
+                    vmax=float(v_true.max()))
+    return Survey(geom, f, v_true, v0, shots)

@@ -81,3 +81,25 @@ def test_argument_validation_without_gpu(fwi_lib):
     n = C.c_size_t()
     assert fwi_lib.zfp_compress_fixed_accuracy(None, 4, 4, 4, 1e-3, None, 0, C.byref(n), None) == _lib.FWI_ERR_ARG
     assert fwi_lib.zfp_decompress(None, 0, None, 4, 4, 4, None) == _lib.FWI_ERR_ARG
+
+
+def test_batch_argument_validation_without_gpu(fwi_lib):
+    from paper_2009_12623_gb300 import _lib
+    g = _lib.Geometry(40, 40, 20, 10.0, 1e-3, 0, 4, 1e-3, 2000.0)
+    ok = _lib.Shot(0, 0, 0, 20, 20, 20, 10, 5, 5, 3, 0, 0, 0, 0)
+    out = C.c_void_p()
+    pol = _lib.Policy(2, 4, 1e-4)
+    create = fwi_lib.fwi_batch_create
+    shots = (_lib.Shot * 1)(ok)
+    assert create(C.byref(g), 0, shots, None, C.byref(pol), 1 << 20, 0, C.byref(out)) == _lib.FWI_ERR_ARG
+    for bad in [_lib.Shot(30, 0, 0, 20, 20, 20, 10, 35, 5, 3, 0, 0, 0, 0),   # window past the grid
+                _lib.Shot(0, 0, 0, 20, 20, 20, 0, 5, 5, 3, 0, 0, 0, 0),     # no time steps
+                _lib.Shot(0, 0, 0, 20, 20, 20, 10, 25, 5, 3, 0, 0, 0, 0),   # source outside the window
+                _lib.Shot(0, 0, 0, 20, 20, 20, 10, 5, 5, 3, 0, 4, 0, 0)]:   # receivers but no array
+        arr = (_lib.Shot * 1)(bad)
+        assert create(C.byref(g), 1, arr, None, C.byref(pol), 1 << 20, 0, C.byref(out)) == _lib.FWI_ERR_ARG
+    for p in [_lib.Policy(3, 2, 0.0), _lib.Policy(4, 2, 0.0), _lib.Policy(2, 0, 0.0)]:
+        assert create(C.byref(g), 1, shots, None, C.byref(p), 1 << 20, 0, C.byref(out)) == _lib.FWI_ERR_ARG
+    assert create(C.byref(g), 1, shots, None, C.byref(pol), 1 << 20, 8, C.byref(out)) == _lib.FWI_ERR_ARG
+    assert fwi_lib.fwi_batch_destroy(None) == _lib.FWI_ERR_ARG
+    assert fwi_lib.fwi_batch_get_stats(None, None) == _lib.FWI_ERR_ARG
