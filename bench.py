@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--no-verify", action="store_true")
     p.add_argument("--arena-gb", type=float, default=0.0,
                    help="checkpoint arena size (0 = all free memory minus the working set)")
+    p.add_argument("--workload", default="overthrust", choices=["overthrust", "batch"],
+                   help="batch: 32-shot survey, batched plan against one call per shot")
+    p.add_argument("--shots", type=int, default=32)
+    p.add_argument("--ckpt-k", type=int, default=10, help="batch workload: checkpoint pair every K steps")
     return p.parse_args()
 
 
@@ -468,10 +472,131 @@ def run_fwi(args):
         pg.destroy_process_group()
 
 
+def run_batch(args):
+    """Survey of `shots` shots on a 600 x 600 x 200 layered model at 20 m
+    (apertures 200-600 cells per side, records 1500-3000 ms at dt = 1.5 ms,
+    10 Hz, 40-cell absorbing layer, receivers every 4th node), every-K
+    compressed checkpoint pairs: one stacked gradient per step, through the
+    batch plan (graph + autotuner) and through one fwi_gradient call per shot."""
+    import numpy as np
+    import torch
+    ws, rank, local, pg = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_12623_gb300 import api, synth
+
+    t_setup = time.perf_counter()
+    sv = synth.batch_survey(nshots=args.shots, seed=rank)
+    g = sv.geom
+    m = torch.from_numpy(synth.slowness2(sv.v0)).to(dev)
+    mt = torch.from_numpy(synth.slowness2(sv.v_true)).to(dev)
+    w = sv.wavelets()
+    d_obs = []
+    for s, wi in zip(sv.shots, w):
+        origin = torch.tensor([s.x0, s.y0, s.z0], dtype=torch.int32, device=dev)
+        rec = (torch.from_numpy(np.asarray(s.rec, np.int32)).to(dev) - origin).contiguous()
+        d_obs.append(api.forward(s.local_geometry(g), mt[s.window].contiguous(), wi,
+                                 (s.src[0] - s.x0, s.src[1] - s.y0, s.src[2] - s.z0), rec))
+    del mt
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    K, atol = args.ckpt_k, args.atol
+    cell_steps = sum(s.nx * s.ny * s.nz * s.nt for s in sv.shots)
+
+    def timed(fn, steps):
+        barrier(pg)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = None
+        for _ in range(steps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(pg)
+        return max_over_ranks(pg, e0.elapsed_time(e1)), out
+
+    # ---- plain path: one fwi_gradient call per shot ----------------------------
+    store = api.CheckpointStore(int((args.arena_gb or 24) * (1 << 30)))
+    g_plain = torch.zeros(g.shape, dtype=torch.float32, device=dev)
+
+    def plain():
+        g_plain.zero_()
+        return api.gradient_per_shot(g, m, sv.shots, w, d_obs, store, mode=api.FWI_CKPT_EVERY_K, k=K,
+                                     atol=atol, grad=g_plain)
+    for _ in range(args.warmup):
+        plain()
+    l0 = api.kernel_launch_count()
+    ms_plain, (_, phi_plain) = timed(plain, args.steps)
+    launches_plain = (api.kernel_launch_count() - l0) // args.steps
+    store.close()
+    torch.cuda.empty_cache()
+
+    # ---- batched plan (persistent multi-shot launches, CUDA graph, autotuner) ----
+    free, _ = torch.cuda.mem_get_info()
+    with api.Batch(g, sv.shots, mode=api.FWI_CKPT_EVERY_K, k=K, atol=atol, arena_bytes=1 << 30) as probe:
+        need = probe.stats()["device_bytes"] - (1 << 30)
+    arena = int(min(free - need - 8 * (1 << 30), 160 * (1 << 30)))
+    b = api.Batch(g, sv.shots, mode=api.FWI_CKPT_EVERY_K, k=K, atol=atol, arena_bytes=arena, graph=True,
+                  tune=True)
+    obs = b.concat(d_obs)
+    g_batch = torch.zeros(g.shape, dtype=torch.float32, device=dev)
+
+    def batched():
+        g_batch.zero_()
+        return b.gradient(m, w, obs, grad=g_batch)
+    t0 = time.perf_counter()
+    batched()  # tunes, captures
+    torch.cuda.synchronize()
+    t_first = time.perf_counter() - t0
+    for _ in range(max(0, args.warmup - 1)):
+        batched()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    l0 = api.kernel_launch_count()
+    ms_batch, (_, phi_batch) = timed(batched, args.steps)
+    launches_batch = (api.kernel_launch_count() - l0) // args.steps
+    clk = clocks.stop()
+    st = b.stats()
+    same = bool(torch.equal(g_batch, g_plain)) and bool(np.array_equal(phi_batch, phi_plain))
+    b.close()
+
+    value = ws * args.shots * args.steps / (ms_batch / 1e3)
+    plain_value = ws * args.shots * args.steps / (ms_plain / 1e3)
+    if rank == 0:
+        line = {"metric": "shot-gradients/s at fixed gradient error vs plain path", "value": value,
+                "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"batched survey: {args.shots} shots on 600x600x200 at 20 m, apertures "
+                                       f"200-600 cells, records 1500-3000 ms at 1.5 ms, 10 Hz, every-{K} "
+                                       f"compressed checkpoint pairs (atol={atol:g})",
+                           "shots": args.shots, "cell_steps_per_gradient": cell_steps,
+                           "l2_flush": "inputs larger than L2 (>= 32 MB fields per shot, GBs per step)"},
+                "plain": {"value": plain_value, "unit": UNIT, "ms_per_step": ms_plain / args.steps,
+                          "gpu_launches_per_step": launches_plain,
+                          "path": "one fwi_gradient call per shot on its window"},
+                "speedup_vs_plain": ms_plain / ms_batch,
+                "same_gradient_bitwise": same,
+                "gpu_launches": launches_batch * args.steps,
+                "plan": {k: st[k] for k in ("zc", "ctas", "zc_adjoint", "ctas_adjoint", "graph_nodes",
+                                            "launches_per_call", "used_bytes", "raw_bytes", "device_bytes")},
+                "first_call_s": t_first, "setup_s": t_setup, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_fwi(args)
 

@@ -7,8 +7,8 @@
  * d_sim = P_r A(m)^-1 P_s^T q_s (Sec. 2, Eq. (2)), the misfit
  * Phi = 1/2 ||d_sim - d_obs||^2 (Eq. (3)) and its gradient with respect to
  * the squared slowness m (Eq. (4)), keeping the forward wavefield as
- * checkpoints (Sec. 1.2) that are compressed with a fixed-accuracy block codec
- * (Sec. 1.3, Fig. 1).
+ * checkpoints (Sec. 1.3) that are compressed with a fixed-accuracy block codec
+ * (Sec. 1.4, Fig. 1).
  *
  * Conventions shared by every call:
  *   - Fields are FP32, C order [nz][ny][nx] (x fastest), unpadded, on the
@@ -60,7 +60,7 @@ typedef struct {
   double vmax;     /* reference velocity of the damping profile, m/s */
 } fwi_geometry;
 
-/* ---- checkpoint policy and schedule (Sec. 1.2) ---------------------------- */
+/* ---- checkpoint policy and schedule (Sec. 1.3) ---------------------------- */
 #define FWI_CKPT_FULL 1    /* keep every forward state u^1..u^N */
 #define FWI_CKPT_EVERY_K 2 /* keep the pair (u^{c-1}, u^c) at c = 0, K, 2K, ...;
                               recompute the states in between during the
@@ -68,7 +68,7 @@ typedef struct {
 #define FWI_CKPT_BINOMIAL 3 /* at most k_or_snaps state pairs at a time, placed by
                                recursive splitting so that the forward steps
                                recomputed are the fewest possible (the
-                               Revolve family of schedules, Sec. 1.2); the
+                               Revolve family of schedules, Sec. 1.3); the
                                pairs are used last-in first-out */
 #define FWI_CKPT_SUBSAMPLE 4 /* the subsampling baseline of Sec. 4.7: keep u^k only for
                                 k = f, 2f, ... (f = k_or_snaps) and apply the imaging
@@ -78,11 +78,11 @@ typedef struct {
   int k_or_snaps; /* K for FWI_CKPT_EVERY_K, snapshot pairs for FWI_CKPT_BINOMIAL,
                      the factor f for FWI_CKPT_SUBSAMPLE */
   double atol;    /* > 0: compress every checkpoint with this absolute error
-                     tolerance (Sec. 1.3); <= 0: raw FP32 copies */
+                     tolerance (Sec. 1.4); <= 0: raw FP32 copies */
 } fwi_ckpt_policy;
 
 /* Actions of a schedule: the "forward, store, backward, load and recompute
- * events" of Sec. 1.2. */
+ * events" of Sec. 1.3. */
 #define FWI_ACT_ADVANCE 1   /* forward step: u^step -> u^{step+1}, record data d^step */
 #define FWI_ACT_STORE 2     /* store the state at `step` (arg = 1: u^step; 2: u^{step-1}, u^step) */
 #define FWI_ACT_RESTORE 3   /* make the stored state at `step` current (arg as for STORE) */
@@ -136,7 +136,7 @@ int fwi_forward(const fwi_geometry* g, const float* d_m, const float* h_wavelet,
                 const float* d_u_prev_init, const float* d_u_cur_init, float* d_u_prev_out,
                 float* d_u_last_out, void* stream);
 
-/* ---- gradient (Sec. 2, Eq. (3)-(4); Sec. 1.2-1.3, Fig. 1) ---------------- */
+/* ---- gradient (Sec. 2, Eq. (3)-(4); Sec. 1.3-1.4, Fig. 1) ---------------- */
 /* Forward sweep storing checkpoints into st per pol, misfit, adjoint sweep
  * decompressing them, imaging condition accumulated as
  *   d_grad += dPhi/dm = -sum_{k=1}^{N} u^k (l_{k-1} - 2 l_k + l_{k+1}) / dt^2
@@ -253,7 +253,7 @@ typedef struct {
 } fwi_batch_stats;
 int fwi_batch_get_stats(const fwi_batch* b, fwi_batch_stats* out);
 
-/* ---- fixed-accuracy codec (Sec. 1.3) -------------------------------------- */
+/* ---- fixed-accuracy codec (Sec. 1.4) -------------------------------------- */
 /* Stream format (shared bit-for-bit with the CPU oracle):
  *   64-byte header (magic "FCZ1", version, nx, ny, nz, minexp, nblocks,
  *   chunk size 32, nchunks, payload words, total bytes, format params),

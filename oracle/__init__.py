@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY: a plain, slow FP64 CPU restatement of what the GPU
 library computes (Kukreja et al., "Lossy Checkpoint Compression in Full
-Waveform Inversion", Sec. 2 Eq. (1)-(4), Sec. 1.2-1.3).  Only ``tests/``,
+Waveform Inversion", Sec. 2 Eq. (1)-(4), Sec. 1.3-1.4).  Only ``tests/``,
 ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline / reference arm
 may import this package.  It shares no code with ``paper_2009_12623_gb300``;
 the C sources here are compiled into ``liboracle.so`` by :func:`build`.

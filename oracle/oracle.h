@@ -17,8 +17,8 @@
  *   Sec. 2, Eq. (2)  d_sim = P_r A(m)^-1 P_s^T q_s
  *   Sec. 2, Eq. (3)  Phi_s(m) = 1/2 || d_sim - d_obs ||^2
  *   Sec. 2, Eq. (4)  grad Phi_s = sum_t u[t] v_tt[t]  (adjoint run backwards)
- *   Sec. 1.2         checkpointing (store / restore / recompute); exact
- *   Sec. 1.3, Fig. 1 lossy compression of every checkpoint (ZFP, fixed accuracy)
+ *   Sec. 1.3         checkpointing (store / restore / recompute); exact
+ *   Sec. 1.4, Fig. 1 lossy compression of every checkpoint (ZFP, fixed accuracy)
  *   Sec. 3           reference problem: 8 Hz Ricker, absorbing layer, dt
  *
  * Parity status of each function is stated beside it ("pinned by ..." names
@@ -54,8 +54,8 @@ typedef struct {
   double vmax;     /* reference velocity of the damping profile, m/s */
 } oracle_geometry;
 
-/* Checkpoint policies (Sec. 1.2).  atol <= 0 stores raw copies; atol > 0
- * stores fixed-accuracy compressed FP32 copies (Sec. 1.3). */
+/* Checkpoint policies (Sec. 1.3).  atol <= 0 stores raw copies; atol > 0
+ * stores fixed-accuracy compressed FP32 copies (Sec. 1.4). */
 #define ORACLE_CKPT_FULL 1    /* keep u^k for every k = 1..N */
 #define ORACLE_CKPT_EVERY_K 2 /* keep (u^{c-1}, u^c) for c = 0, K, 2K, ... */
 #define ORACLE_CKPT_BINOMIAL 3 /* at most k state pairs at a time, placed to minimise recomputation */
@@ -66,7 +66,7 @@ typedef struct {
   double atol;
 } oracle_policy;
 
-/* Checkpoint-schedule actions (Sec. 1.2: forward, store, backward, load and
+/* Checkpoint-schedule actions (Sec. 1.3: forward, store, backward, load and
  * recompute events). */
 #define ORACLE_ACT_ADVANCE 1 /* forward step: u^{step} -> u^{step+1}, recording data */
 #define ORACLE_ACT_STORE 2   /* store checkpoint at step (arg = levels: 1 or 2) */
@@ -160,7 +160,7 @@ int oracle_gradient_batch(const oracle_geometry* g, const double* m, int nshots,
  * snapshot slots, serving adjoint steps a+n .. a+1 costs
  *   cost(n, 0) = n(n+1)/2 (restart from a for every step),
  *   cost(n, s) = min(cost(n, 0), min_{0<m<n} m + cost(n-m, s-1) + cost(m, s)),
- * the recursive splitting of Sec. 1.2's Revolve-family schedules; the
+ * the recursive splitting of Sec. 1.3's Revolve-family schedules; the
  * smallest minimising m is taken.  Pinned: the table equals Griewank's
  * closed-form minimum and the schedule's raw result equals full history. */
 long long oracle_binomial_cost(int n, int s);
@@ -169,7 +169,7 @@ long long oracle_binomial_cost(int n, int s);
 int oracle_ckpt_schedule(int nt, const oracle_policy* pol, oracle_action* out,
                          size_t cap, size_t* n_out);
 
-/* ---- fixed-accuracy block codec (Sec. 1.3; format defined by this project) */
+/* ---- fixed-accuracy block codec (Sec. 1.4; format defined by this project) */
 
 /* Worst-case stream size in bytes for an nx*ny*nz field. */
 size_t oracle_zfp_max_bytes(int nx, int ny, int nz);

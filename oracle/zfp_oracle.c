@@ -3,7 +3,7 @@
  *
  * The paper compresses every checkpoint with ZFP in fixed-accuracy mode: the
  * caller fixes an absolute error tolerance atol and every decompressed value
- * stays within it (Sec. 1.3; Sec. 4.2 and the appendix figure on direct
+ * stays within it (Sec. 1.4; Sec. 4.2 and the appendix figure on direct
  * compression report L_inf below atol).  The paper does not describe ZFP's
  * internals, so this project defines its own ZFP-style format from the
  * published structure of that method (4x4x4 blocks, a common block exponent,

@@ -6,7 +6,7 @@ forward wavefield as (optionally compressed) checkpoints in a store.  The
 backward pass receives dL/dd for whatever loss the caller built and runs the
 reverse sweep from those checkpoints (fwi_adjoint_store), returning
 dL/dm = J^T dL/dd -- the imaging condition of Eq. (4) with dL/dd as adjoint
-source.  Lossy checkpoint compression (Sec. 1.3) thus replaces full-history
+source.  Lossy checkpoint compression (Sec. 1.4) thus replaces full-history
 storage in an ordinary PyTorch training loop.
 """
 from __future__ import annotations

@@ -429,8 +429,7 @@ int run(fwi_batch* B, int phases, const float* d_m, const float* d_obs, const fl
 // plan's own fields for a few steps of the forward and of the adjoint
 // kernel, and keep the fastest of each.
 int tune(fwi_batch* B, cudaStream_t s) {
-  const int cap = stencil_multi_capacity();
-  if (cap <= 0) return FWI_ERR_CUDA;
+  if (stencil_multi_capacity(false) <= 0) return FWI_ERR_CUDA;
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -438,9 +437,6 @@ int tune(fwi_batch* B, cudaStream_t s) {
   int nz = 1;
   for (const BShot& sh : B->shots) nz = std::max(nz, sh.G.nz);
   std::vector<int> zcs = {0, nz, (nz + 1) / 2, (nz + 2) / 3, (nz + 3) / 4, 64, 48, 32, 24, 16};
-  std::vector<int> grids;
-  for (int m = 1; m * sms <= cap; ++m) grids.push_back(m * sms);
-  if (grids.empty()) grids.push_back(cap);
   std::sort(zcs.begin(), zcs.end());
   zcs.erase(std::unique(zcs.begin(), zcs.end()), zcs.end());
   cudaEvent_t ta, tb;
@@ -452,6 +448,10 @@ int tune(fwi_batch* B, cudaStream_t s) {
   const int reps = 3;
   int rc = FWI_OK;
   for (int adj = 0; adj < 2 && rc == FWI_OK; ++adj) {
+    const int cap = stencil_multi_capacity(adj != 0);
+    std::vector<int> grids;
+    for (int m = 1; m * sms <= cap; ++m) grids.push_back(m * sms);
+    if (grids.empty()) grids.push_back(cap);
     float best = 1e30f;
     int bz = 0, bg = cap;
     for (int zc : zcs) {
@@ -616,7 +616,7 @@ int fwi_batch_create(const fwi_geometry* g, int nshots, const fwi_shot* h_shots,
     if (!shot_ok(g, h_shots[i])) return FWI_ERR_ARG;
     if (h_shots[i].nrec > 0 && !d_rec_ijk) return FWI_ERR_ARG;
   }
-  if (stencil_multi_capacity() <= 0) return FWI_ERR_CUDA;
+  if (stencil_multi_capacity(false) <= 0) return FWI_ERR_CUDA;
   fwi_batch* B = new fwi_batch();
   B->g = *g;
   B->pol = *pol;
@@ -736,7 +736,8 @@ int fwi_batch_create(const fwi_geometry* g, int nshots, const fwi_shot* h_shots,
   }
   if (flags_h) return fail(FWI_ERR_ARG);  // a receiver outside its shot's aperture
   // default launch shape: deep tiles while the tile list still fills the GPU
-  B->ctas = B->ctas_adj = stencil_multi_capacity();
+  B->ctas = stencil_multi_capacity(false);
+  B->ctas_adj = stencil_multi_capacity(true);
   int nz = 1;
   long cols = 0;
   for (const BShot& sh : B->shots) {

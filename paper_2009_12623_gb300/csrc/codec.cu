@@ -1,4 +1,4 @@
-// Fixed-accuracy block codec for FP32 wavefields on sm_103a (Sec. 1.3 of
+// Fixed-accuracy block codec for FP32 wavefields on sm_103a (Sec. 1.4 of
 // Kukreja et al.: every checkpoint is compressed with an absolute error
 // tolerance atol; the format is this project's ZFP-style design).
 //

@@ -157,8 +157,9 @@ struct StencilField {
   float* grad;            // adjoint: gradient accumulator
   int zc;                 // z-chunk of the tiles (0: automatic)
 };
-// Resident CTAs of the multi-field kernel on the whole GPU (0 on failure).
-int stencil_multi_capacity();
+// Resident CTAs of the multi-field forward or adjoint kernel on the whole GPU
+// (0 on failure).
+int stencil_multi_capacity(bool adjoint);
 // One persistent launch over the tiles of all fields; ctas <= 0 = resident capacity.
 cudaError_t stencil_multi_launch(bool adjoint, int nfields, const StencilParams* const* p,
                                  const StencilField* f, float weight, int ctas, cudaStream_t s);

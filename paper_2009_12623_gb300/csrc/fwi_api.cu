@@ -1,6 +1,6 @@
 // C-ABI entry points of libfwi (declared in include/fwi.h): checkpoint store,
 // checkpoint schedule, forward modelling, the checkpointed gradient of
-// Kukreja et al. (Sec. 2 Eq. (2)-(4), Sec. 1.2-1.3, Fig. 1), the codec calls
+// Kukreja et al. (Sec. 2 Eq. (2)-(4), Sec. 1.3-1.4, Fig. 1), the codec calls
 // and the FP64 reductions.  Host code here only validates arguments, owns
 // memory and sequences the kernels of stencil.cu and codec.cu on the caller's
 // stream; every arithmetic step of the path runs on the GPU.
@@ -151,7 +151,7 @@ bool in_grid(const fwi_geometry* g, int i, int j, int k) {
   return i >= 0 && j >= 0 && k >= 0 && i < g->nx && j < g->ny && k < g->nz;
 }
 
-// Schedule generator: the event list of Sec. 1.2 for the two policies.
+// Schedule generator: the event list of Sec. 1.3 for the two policies.
 struct Sched {
   std::vector<fwi_action> a;
   void add(int kind, int step, int arg) { a.push_back(fwi_action{kind, step, arg}); }

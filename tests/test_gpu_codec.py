@@ -1,5 +1,5 @@
 """GPU codec parity with the oracle: compressed streams bit-exact, decoded
-values bit-exact (Sec. 1.3 fixed-accuracy compression of checkpoints)."""
+values bit-exact (Sec. 1.4 fixed-accuracy compression of checkpoints)."""
 import numpy as np
 import pytest
 import torch

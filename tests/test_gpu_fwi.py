@@ -1,5 +1,5 @@
 """GPU forward sweep, checkpointed gradient and reductions vs the FP64 oracle
-(Sec. 2 Eq. (2)-(4); Sec. 1.2-1.3).  Tolerance: FP32 fields within 1e-4
+(Sec. 2 Eq. (2)-(4); Sec. 1.3-1.4).  Tolerance: FP32 fields within 1e-4
 relative L2 of the FP64 oracle."""
 import numpy as np
 import pytest
@@ -176,7 +176,7 @@ def test_subsampling_matches_oracle(cuda, oracle):
 
 @pytest.mark.parametrize("k", [1, 4, 10, 33, 500])
 def test_every_k_raw_bitwise_equals_full_history(cuda, two_layer, k):
-    """Checkpointing alone is bitwise exact (Sec. 1.2) on the GPU too."""
+    """Checkpointing alone is bitwise exact (Sec. 1.3) on the GPU too."""
     shot, d_obs = two_layer
     g_full, phi_full, _ = _grad(cuda, shot, d_obs, 1)
     g_k, phi_k, _ = _grad(cuda, shot, d_obs, 2, k=k)

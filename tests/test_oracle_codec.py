@@ -1,4 +1,4 @@
-"""Pins of the oracle's fixed-accuracy codec (Sec. 1.3; the appendix figure on
+"""Pins of the oracle's fixed-accuracy codec (Sec. 1.4; the appendix figure on
 direct compression: L_inf of the error stays below atol)."""
 import json
 import os

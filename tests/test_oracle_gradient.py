@@ -1,5 +1,5 @@
 """Pins of the oracle's adjoint sweep, gradient and checkpoint schedules
-(Sec. 2 Eq. (2)-(4); Sec. 1.2 -- checkpointing alone is bitwise exact)."""
+(Sec. 2 Eq. (2)-(4); Sec. 1.3 -- checkpointing alone is bitwise exact)."""
 import numpy as np
 import pytest
 
@@ -96,7 +96,7 @@ def test_gradient_zero_at_true_model(oracle):
 
 @pytest.mark.parametrize("k", [1, 3, 7, 10, NT, NT + 5])
 def test_every_k_raw_bitwise_equals_full_history(oracle, k):
-    """Checkpointing alone keeps the result bitwise identical (Sec. 1.2)."""
+    """Checkpointing alone keeps the result bitwise identical (Sec. 1.3)."""
     g, m, q, src, rec = _case(oracle)
     dobs = _obs(oracle, g, m, q, src, rec)
     g_full, phi_full, d_full, _ = oracle.gradient(g, m, q, src, rec, dobs, mode=oracle.CKPT_FULL)
