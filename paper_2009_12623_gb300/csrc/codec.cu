@@ -36,6 +36,9 @@ constexpr int kWarps = 4;                                       // chunks per CT
 #ifndef FWI_ENC_MIN_CTAS
 #define FWI_ENC_MIN_CTAS 4  // resident CTAs per SM the staged encoder is compiled for
 #endif
+#ifndef FWI_DEC_MIN_CTAS
+#define FWI_DEC_MIN_CTAS 4  // the same for the decoder
+#endif
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -281,21 +284,52 @@ __device__ __forceinline__ void gather_block(const EncArgs& a, long blk, uint32_
   }
 }
 
+// Shared memory of the staged encoder, per warp: the low and high halves of
+// the 32 plane masks of each lane's block ([plane][lane] u32 arrays,
+// conflict-free), and a buffer in which the chunk's words are assembled when
+// they fit (always for real wavefields; a larger chunk is assembled directly
+// in its global staging slot instead).
+constexpr int kAsmWords = 512;
+constexpr int kEncSmemPerWarp = 2 * 32 * 32 * 4 + (kAsmWords + 1) * 8;
+constexpr int kEncSmem = kWarps * kEncSmemPerWarp;
+
+struct SmemPlanes {  // plane b of one lane's block
+  const uint32_t* lo;
+  const uint32_t* hi;
+  __device__ __forceinline__ uint64_t operator()(int b) const {
+    return (uint64_t)lo[b * 32] | ((uint64_t)hi[b * 32] << 32);
+  }
+};
+
 __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_ENC_MIN_CTAS) k_encode_stage(EncArgs a, StageArgs st) {
-  __shared__ unsigned long long sbuf_all[kWarps][kWordsMax + 1];
+  extern __shared__ unsigned long long enc_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned long long* sbuf = sbuf_all[wid];
+  unsigned char* base = reinterpret_cast<unsigned char*>(enc_smem) + (size_t)wid * kEncSmemPerWarp;
+  uint32_t* lo = reinterpret_cast<uint32_t*>(base);  // [32][32]
+  uint32_t* hi = lo + 32 * 32;
+  unsigned long long* sbuf = reinterpret_cast<unsigned long long*>(hi + 32 * 32);
   const long chunk = (long)blockIdx.x * kWarps + wid;
   if (chunk >= a.nchunks) return;  // whole warp
   const long blk = chunk * ZC_CHUNK + lane;
   const bool valid = blk < a.nblocks;
-  uint32_t u[64];
   int planes = 0, emax = 0, nbits = 0;
   if (valid) {
+    uint32_t u[64];
     gather_block(a, blk, u);
-    if (!quantise(u, a.minexp, emax, planes)) atomicOr(a.status, ST_NONFINITE);
-    nbits = count_bits(u, planes);
+    if (!quantise_coeffs(u, a.minexp, emax, planes)) atomicOr(a.status, ST_NONFINITE);
+    if (planes) {  // a block with no coded plane is the single bit 0: nothing to transpose
+      transpose32(u);
+#pragma unroll
+      for (int b = 0; b < 32; ++b)
+        if (b >= 32 - planes) lo[b * 32 + lane] = u[b];
+      transpose32(u + 32);
+#pragma unroll
+      for (int b = 0; b < 32; ++b)
+        if (b >= 32 - planes) hi[b * 32 + lane] = u[32 + b];
+    }
   }
+  const SmemPlanes mine{lo + lane, hi + lane};
+  if (valid) nbits = count_bits_mem(mine, planes);
   unsigned incl = (unsigned)nbits;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -305,16 +339,18 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_ENC_MIN_CTAS) k_encode_
   const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
   const unsigned my_off = incl - (unsigned)nbits;
   const unsigned W = (total + 63u) / 64u;
-  for (unsigned w = lane; w < W; w += 32) sbuf[w] = 0ull;
+  unsigned long long* dst = st.stage + chunk * (long)kWordsMax;
+  unsigned long long* buf = W <= (unsigned)kAsmWords ? sbuf : dst;  // warp-uniform
+  for (unsigned w = lane; w < W; w += 32) buf[w] = 0ull;
   __syncwarp();
   if (valid) {
-    SWriter wr{sbuf, 0ull, (int)(my_off & 63u), (int)(my_off >> 6)};
-    emit(wr, u, emax, planes);
+    SWriter wr{buf, 0ull, (int)(my_off & 63u), (int)(my_off >> 6)};
+    emit_mem(wr, mine, emax, planes);
     wr.flush();
   }
   __syncwarp();
-  unsigned long long* dst = st.stage + chunk * (long)kWordsMax;
-  for (unsigned w = lane; w < W; w += 32) dst[w] = sbuf[w];
+  if (buf == sbuf)
+    for (unsigned w = lane; w < W; w += 32) dst[w] = sbuf[w];
   if (valid) {
     const unsigned long long base = a.base ? *a.base : 0ull;
     const unsigned long long avail = a.limit > base ? a.limit - base : 0ull;
@@ -449,17 +485,20 @@ struct DecArgs {
   int* status;
 };
 
-// Bit reader over a chunk staged in shared memory (two zero words follow the
-// chunk, so a peek at the end stays inside the buffer).
+// Bit reader over a chunk's words (staged in shared memory, or in global
+// memory for a chunk larger than the staging buffer); words at index >= nw
+// read as zero, so a peek at the end never leaves the chunk.
 struct SReader {
   const unsigned long long* buf;
   long pos;
   long end;
+  long nw;
   __device__ __forceinline__ unsigned long long peek() const {
     const long w = pos >> 6;
     const int o = (int)(pos & 63);
-    unsigned long long v = buf[w] >> o;
-    if (o) v |= buf[w + 1] << (64 - o);
+    unsigned long long v = w < nw ? buf[w] : 0ull;
+    v >>= o;
+    if (o && w + 1 < nw) v |= buf[w + 1] << (64 - o);
     return v;
   }
 };
@@ -469,10 +508,27 @@ __device__ __forceinline__ unsigned long long get_u64(const uint8_t* p) {
   return *reinterpret_cast<const unsigned long long*>(p);
 }
 
-__global__ void __launch_bounds__(ZC_CHUNK * kWarps, 4) k_decode(DecArgs a) {
-  __shared__ unsigned long long sbuf_all[kWarps][kWordsMax + 2];
+// Shared memory of the decoder, per warp: the plane masks of each lane's
+// block ([plane][lane] low / high halves) and the chunk's words when they fit.
+constexpr int kDecSmemPerWarp = 2 * 32 * 32 * 4 + (kAsmWords + 2) * 8;
+constexpr int kDecSmem = kWarps * kDecSmemPerWarp;
+
+struct SmemSink {  // plane b of one lane's block
+  uint32_t* lo;
+  uint32_t* hi;
+  __device__ __forceinline__ void operator()(int b, uint64_t m) const {
+    lo[b * 32] = (uint32_t)m;
+    hi[b * 32] = (uint32_t)(m >> 32);
+  }
+};
+
+__global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(DecArgs a) {
+  extern __shared__ unsigned long long dec_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned long long* sbuf = sbuf_all[wid];
+  unsigned char* wbase = reinterpret_cast<unsigned char*>(dec_smem) + (size_t)wid * kDecSmemPerWarp;
+  uint32_t* lo = reinterpret_cast<uint32_t*>(wbase);  // [32][32]
+  uint32_t* hi = lo + 32 * 32;
+  unsigned long long* sbuf = reinterpret_cast<unsigned long long*>(hi + 32 * 32);
   const long chunk = (long)blockIdx.x * kWarps + wid;
   if (chunk >= a.nchunks) return;  // whole warp
   const unsigned long long base = a.base ? *a.base : 0ull;
@@ -511,10 +567,12 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, 4) k_decode(DecArgs a) {
   const long blk = chunk * ZC_CHUNK + lane;
   const bool valid = blk < a.nblocks;
   const int len = valid ? (int)*reinterpret_cast<const uint16_t*>(in + a.length_table + 2ull * blk) : 0;
-  // stage the chunk's words and scan the block lengths
+  // stage the chunk's words (when they fit) and scan the block lengths
   const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in + a.payload) + first;
-  for (unsigned long long w = lane; w < words; w += 32) sbuf[w] = __ldg(src + w);
-  if (lane < 2) sbuf[words + lane] = 0ull;
+  const bool staged = words <= (unsigned long long)kAsmWords;  // warp-uniform
+  if (staged) {
+    for (unsigned long long w = lane; w < words; w += 32) sbuf[w] = __ldg(src + w);
+  }
   unsigned incl = (unsigned)len;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -529,15 +587,24 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, 4) k_decode(DecArgs a) {
   }
   if (!valid) return;
   const long start = (long)(incl - (unsigned)len);
-  SReader rd{sbuf, start, start + len};
-  uint32_t u[64];
+  SReader rd{staged ? sbuf : src, start, start + len, (long)words};
   int emax = 0, planes = 0;
-  if (!decode_planes(rd, minexp, u, emax, planes) || rd.pos != rd.end) {
+  SmemSink sink{lo + lane, hi + lane};
+  if (!decode_planes_mem(rd, minexp, sink, emax, planes) || rd.pos != rd.end) {
     atomicOr(a.status, ST_CORRUPT);
     return;
   }
   float v[64];
-  dequantise(u, emax, planes, v);
+  {
+    uint32_t u[64];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      const bool coded = b >= 32 - planes;
+      u[b] = coded ? lo[b * 32 + lane] : 0u;
+      u[32 + b] = coded ? hi[b * 32 + lane] : 0u;
+    }
+    dequantise(u, emax, planes, v);
+  }
   const long bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
   const long xb = 4 * bx;
   const bool vec = a.vec_ok && xb + 3 < a.nx;
@@ -635,7 +702,13 @@ cudaError_t zfp_encode_launch(const float* in, Grid g, int minexp, uint8_t* out,
   cudaError_t e = cudaMemsetAsync(st.tile_sum, 0, ntiles * 8, s);
   if (e != cudaSuccess) return e;
   const int ps = prof_begin(KC_ZFP_ENCODE, s);
-  k_encode_stage<<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, 0, s>>>(a, st);
+  static bool smem_set = false;  // one attribute call per process (same value on every device)
+  if (!smem_set) {
+    e = cudaFuncSetAttribute(k_encode_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
+    if (e != cudaSuccess) return e;
+    smem_set = true;
+  }
+  k_encode_stage<<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, kEncSmem, s>>>(a, st);
   k_encode_compact<<<(unsigned)ntiles, 256, 0, s>>>(a, st);
   k_encode_place<<<(unsigned)((a.nchunks + 7) / 8), 256, 0, s>>>(a, st);
   prof_end(ps, s);
@@ -688,8 +761,14 @@ cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_bas
   a.length_table = L.length_table;
   a.payload = L.payload;
   a.status = d_status;
+  static bool smem_set = false;  // one attribute call per process (same value on every device)
+  if (!smem_set) {
+    const cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmem);
+    if (e != cudaSuccess) return e;
+    smem_set = true;
+  }
   const int ps = prof_begin(KC_ZFP_DECODE, s);
-  k_decode<<<(unsigned)((L.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, 0, s>>>(a);
+  k_decode<<<(unsigned)((L.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, kDecSmem, s>>>(a);
   prof_end(ps, s);
   count_launch();
   return cudaGetLastError();

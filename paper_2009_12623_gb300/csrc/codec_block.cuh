@@ -174,7 +174,17 @@ FZ_HD uint64_t plane(const uint32_t* u, int b) {
 // FP32 bit patterns of a block -> 32 plane masks (u[b] | u[32+b] << 32 is
 // plane b), block exponent and coded-plane count.  Returns false (and codes
 // the block as zero) when the block holds NaN or Inf.
+FZ_HD bool quantise_coeffs(uint32_t* u, int minexp, int& emax, int& planes);
 FZ_HD bool quantise(uint32_t* u, int minexp, int& emax, int& planes) {
+  const bool finite = quantise_coeffs(u, minexp, emax, planes);
+  transpose32(u);
+  transpose32(u + 32);
+  return finite;
+}
+
+// The same up to the negabinary coefficients in sequency order (u[p] is
+// coefficient p); the caller transposes the two halves into plane masks.
+FZ_HD bool quantise_coeffs(uint32_t* u, int minexp, int& emax, int& planes) {
   uint32_t maxbits = 0;
 #pragma unroll
   for (int i = 0; i < 64; ++i) maxbits = maxbits > (u[i] & 0x7fffffffu) ? maxbits : (u[i] & 0x7fffffffu);
@@ -210,8 +220,6 @@ FZ_HD bool quantise(uint32_t* u, int minexp, int& emax, int& planes) {
   for (int p = 0; p < 64; ++p) c[p] = (u[perm_at(p)] + kNB) ^ kNB;
 #pragma unroll
   for (int p = 0; p < 64; ++p) u[p] = c[p];
-  transpose32(u);
-  transpose32(u + 32);
   return finite;
 }
 
@@ -228,6 +236,22 @@ FZ_HD int count_bits(const uint32_t* u, int planes) {
       nbits += nend + popc64(r) + (nend < 64 ? 1 : 0);
       n = nend;
     }
+  }
+  return nbits;
+}
+
+// The same count with the plane masks in memory: P(b) returns plane b (a
+// rolled loop: small code for the instruction cache).
+template <class P>
+FZ_HD int count_bits_mem(const P& pl, int planes) {
+  if (planes == 0) return 1;
+  int nbits = 9, n = 0;
+  for (int b = 31; b >= 32 - planes; --b) {
+    const uint64_t m = pl(b);
+    const uint64_t r = n < 64 ? (m >> n) : 0ull;
+    const int nend = r ? 64 - clz64(m) : n;
+    nbits += nend + popc64(r) + (nend < 64 ? 1 : 0);
+    n = nend;
   }
   return nbits;
 }
@@ -264,6 +288,37 @@ FZ_HD void emit(W& w, const uint32_t* u, int emax, int planes) {
         n += j + 1;
         r = (j + 1 < 64) ? (r >> (j + 1)) : 0ull;
       }
+    }
+  }
+}
+
+// emit with the plane masks in memory (P(b) returns plane b).
+template <class W, class P>
+FZ_HD void emit_mem(W& w, const P& pl, int emax, int planes) {
+  if (planes == 0) {
+    w.put(0ull, 1);
+    return;
+  }
+  w.put(1ull | ((uint64_t)(emax + 127) << 1), 9);
+  int n = 0;
+  for (int b = 31; b >= 32 - planes; --b) {
+    const uint64_t m = pl(b);
+    if (n > 0) w.put(n < 64 ? (m & ((1ull << n) - 1ull)) : m, n);
+    uint64_t r = n < 64 ? (m >> n) : 0ull;
+    while (n < 64) {
+      if (!r) {
+        w.put(0ull, 1);
+        break;
+      }
+      const int j = ctz64(r);
+      if (j < 63) {
+        w.put(1ull | (1ull << (j + 1)), j + 2);  // group bit, then the run up to the 1
+      } else {
+        w.put(1ull, 1);
+        w.put(1ull << j, j + 1);
+      }
+      n += j + 1;
+      r = (j + 1 < 64) ? (r >> (j + 1)) : 0ull;
     }
   }
 }
@@ -325,6 +380,49 @@ FZ_HD bool decode_planes(R& rd, int minexp, uint32_t* u, int& emax, int& planes)
     }
   }
   return ok;
+}
+
+// decode_planes with a rolled plane loop: plane b goes to sink(b, mask) for
+// every coded plane (uncoded planes are left to the caller).
+template <class R, class K>
+FZ_HD bool decode_planes_mem(R& rd, int minexp, K& sink, int& emax, int& planes) {
+  emax = 0;
+  planes = 0;
+  if (rd.pos + 1 > rd.end) return false;
+  const uint64_t hdr = rd.peek();
+  if (!(hdr & 1ull)) {
+    rd.pos += 1;
+    return true;
+  }
+  if (rd.pos + 9 > rd.end) return false;
+  emax = (int)((hdr >> 1) & 0xffull) - 127;
+  rd.pos += 9;
+  planes = planes_for(emax, minexp);
+  if (planes == 0) return false;
+  int n = 0;
+  for (int b = 31; b >= 32 - planes; --b) {
+    uint64_t m = 0ull;
+    if (n > 0) {
+      if (rd.pos + n > rd.end) return false;
+      const uint64_t v = rd.peek();
+      m = n < 64 ? (v & ((1ull << n) - 1ull)) : v;
+      rd.pos += n;
+    }
+    while (n < 64) {
+      if (rd.pos + 1 > rd.end) return false;
+      const uint64_t t = rd.peek();
+      rd.pos += 1;
+      if (!(t & 1ull)) break;
+      const uint64_t pk = rd.peek();
+      const int j = pk ? ctz64(pk) : 64;
+      if (j >= 64 - n || rd.pos + j + 1 > rd.end) return false;
+      rd.pos += j + 1;
+      m |= 1ull << (n + j);
+      n += j + 1;
+    }
+    sink(b, m);
+  }
+  return true;
 }
 
 // Plane masks -> FP32 values: one rounding of q 2^(emax - S).
