@@ -46,8 +46,10 @@ def parse():
     p.add_argument("--no-verify", action="store_true")
     p.add_argument("--arena-gb", type=float, default=0.0,
                    help="checkpoint arena size (0 = all free memory minus the working set)")
-    p.add_argument("--workload", default="overthrust", choices=["overthrust", "batch"],
-                   help="batch: 32-shot survey, batched plan against one call per shot")
+    p.add_argument("--workload", default="overthrust", choices=["overthrust", "batch", "fwi"],
+                   help="batch: 32-shot survey, batched plan against one call per shot; "
+                        "fwi: 16-shot inversion through autograd, batched against per shot")
+    p.add_argument("--iters", type=int, default=10, help="fwi workload: descent iterations per path")
     p.add_argument("--shots", type=int, default=32)
     p.add_argument("--ckpt-k", type=int, default=10, help="batch workload: checkpoint pair every K steps")
     return p.parse_args()
@@ -591,12 +593,101 @@ def run_batch(args):
         pg.destroy_process_group()
 
 
+def run_fwi_inversion(args):
+    """Differentiable FWI: 300 x 300 x 150 at 20 m, layered model with three
+    +-8% Gaussian anomalies, 16 shots on a 4 x 4 grid, 2000 ms at 10 Hz,
+    full-history checkpoints compressed at atol; `iters` steepest-descent
+    iterations through autograd, once with one gradient call per shot and once
+    through a batch plan (graph + autotuner).  value = shot-gradients/s of the
+    batched path."""
+    import math
+    import numpy as np
+    import torch
+    ws, rank, local, pg = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_12623_gb300 import api, invert, synth
+
+    nx, ny, nz, h, nshots = 300, 300, 150, 20.0, 16
+    nbl = min(20, nz // 6)
+    v = synth.layered_velocity(nx, ny, nz, seed=1, water=nbl + 5)
+    v_true = synth.add_anomalies(v, seed=2, amplitude=0.08)
+    v0 = synth.smooth(v_true, 4.0)
+    vmax = float(v_true.max())
+    dt = 0.4 * h / vmax
+    nt = int(round(2.0 / dt))
+    geom = api.Geometry(nx=nx, ny=ny, nz=nz, h=h, dt=dt, nt=nt, nbl=nbl, vmax=vmax)
+    w = synth.wavelet(nt, dt, 10.0)
+    zr = nbl + 2
+    X, Y = np.meshgrid(np.arange(nbl, nx - nbl, 2), np.arange(nbl, ny - nbl, 2))
+    rec_np = np.stack([X.ravel(), Y.ravel(), np.full(X.size, zr)], 1).astype(np.int32)
+    rec = torch.from_numpy(rec_np).to(dev)
+    side = int(math.ceil(math.sqrt(nshots)))
+    sxs = np.linspace(nbl + 10, nx - nbl - 10, side).astype(int)
+    srcs = [(int(sxs[i % side]), int(sxs[i // side]), zr) for i in range(nshots)]
+    mt = torch.from_numpy(synth.slowness2(v_true)).to(dev)
+    d_obs = [api.forward(geom, mt, w, s, rec) for s in srcs]
+    del mt
+    c0 = torch.from_numpy(v0).to(dev)
+    ct = torch.from_numpy(v_true).to(dev)
+    interior = torch.zeros_like(c0)
+    interior[nbl:nz - nbl, nbl:ny - nbl, nbl:nx - nbl] = 1.0
+    atol = args.atol
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    shots = [(geom, w, s, rec) for s in srcs]
+    invert.invert(c0, shots, d_obs, iters=1, atol=atol, mask=interior)  # warm-up
+    ms_plain, (c_plain, h_plain) = timed(lambda: invert.invert(c0, shots, d_obs, iters=args.iters, atol=atol,
+                                                               mask=interior))
+    torch.cuda.empty_cache()
+    specs = [api.ShotSpec(0, 0, 0, nx, ny, nz, nt, s, rec_np) for s in srcs]
+    with api.Batch(geom, specs, mode=api.FWI_CKPT_FULL, atol=atol, arena_bytes=96 << 30, graph=True,
+                   tune=True) as plan:
+        obs = plan.concat(d_obs)
+        invert.invert_batched(c0, plan, [w] * nshots, obs, iters=1, mask=interior)  # tunes, captures
+        ms_batch, (c_batch, h_batch) = timed(lambda: invert.invert_batched(c0, plan, [w] * nshots, obs,
+                                                                           iters=args.iters, mask=interior))
+        st = plan.stats()
+    err = lambda c: float(torch.linalg.vector_norm(c - ct))
+    value = nshots * args.iters / (ms_batch / 1e3)
+    line = {"metric": "shot-gradients/s at fixed gradient error vs plain path (autograd inversion)",
+            "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.iters, "warmup": 1,
+            "ms_per_step": ms_batch / args.iters, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"differentiable FWI: {nx}x{ny}x{nz} at {h:.0f} m, layered + 3 anomalies (+-8%), "
+                                   f"{nshots} shots, nt={nt} (dt={dt * 1e3:.3f} ms, 2000 ms), 10 Hz, "
+                                   f"full-history checkpoints at atol={atol:g}, steepest descent",
+                       "iterations": args.iters},
+            "plain": {"value": nshots * args.iters / (ms_plain / 1e3), "unit": UNIT,
+                      "ms_per_step": ms_plain / args.iters, "path": "autograd, one gradient call per shot"},
+            "speedup_vs_plain": ms_plain / ms_batch,
+            "misfit_batched": h_batch, "misfit_plain": h_plain,
+            "model_error": {"start": err(c0), "batched": err(c_batch), "plain": err(c_plain)},
+            "plan": {k: st[k] for k in ("zc", "ctas", "zc_adjoint", "ctas_adjoint", "graph_nodes",
+                                        "used_bytes", "raw_bytes")}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "fwi":
+        run_fwi_inversion(args)
     else:
         run_fwi(args)
 

@@ -360,6 +360,8 @@ class Batch:
         self.rec = rec.to(dev)
         self.device = dev
         pol = _lib.Policy(mode, k, atol)
+        self.graph = graph
+        self._staged = {}
         flags = (_lib.FWI_BATCH_GRAPH if graph else 0) | (_lib.FWI_BATCH_TUNE if tune else 0)
         h = C.c_void_p()
         g = geom.cstruct()
@@ -388,16 +390,34 @@ class Batch:
             raise ValueError("wavelets shorter than the shots' record lengths")
         return np.ascontiguousarray(w)
 
+    def _stage(self, name: str, src: torch.Tensor | None, shape) -> torch.Tensor:
+        """Plan-owned tensor (same storage on every call, so that a captured
+        graph is replayed), filled from src when given."""
+        t = self._staged.get(name)
+        if t is None:
+            t = torch.empty(shape, dtype=torch.float32, device=self.device)
+            self._staged[name] = t
+        if src is not None:
+            t.copy_(src.reshape(t.shape))
+        return t
+
     def gradient(self, m: torch.Tensor, wavelets, d_obs: torch.Tensor, grad: torch.Tensor | None = None):
         """fwi_batch_gradient: (grad += sum_s dPhi_s/dm, misfits (nshots,) FP64)."""
         w = self._wavelets(wavelets)
         if grad is None:
             grad = torch.zeros(self.geom.shape, dtype=torch.float32, device=m.device)
         phi = (C.c_double * max(len(self.shots), 1))()
+        g = grad
+        if self.graph:  # graph replay needs the same device pointers on every call
+            m = self._stage("m", m, self.geom.shape)
+            d_obs = self._stage("obs", d_obs, (max(self.n_obs, 1),))
+            g = self._stage("grad", None, self.geom.shape).zero_()
         st = _lib.load().fwi_batch_gradient(self.handle, _dev(m, torch.float32, "m"), w.ctypes.data,
-                                            _dev(d_obs, torch.float32, "d_obs"), _dev(grad, torch.float32, "grad"),
+                                            _dev(d_obs, torch.float32, "d_obs"), _dev(g, torch.float32, "grad"),
                                             phi, _stream())
         check("fwi_batch_gradient", st)
+        if g is not grad:
+            grad += g
         return grad, np.array(phi[: len(self.shots)])
 
     def forward(self, m: torch.Tensor, wavelets, out: torch.Tensor | None = None) -> torch.Tensor:
@@ -405,9 +425,15 @@ class Batch:
         w = self._wavelets(wavelets)
         if out is None:
             out = torch.empty(max(self.n_obs, 1), dtype=torch.float32, device=m.device)
+        d = out
+        if self.graph:
+            m = self._stage("m", m, self.geom.shape)
+            d = self._stage("d", None, (max(self.n_obs, 1),))
         st = _lib.load().fwi_batch_forward(self.handle, _dev(m, torch.float32, "m"), w.ctypes.data,
-                                           _dev(out, torch.float32, "d"), _stream())
+                                           _dev(d, torch.float32, "d"), _stream())
         check("fwi_batch_forward", st)
+        if d is not out:
+            out.copy_(d)
         return out[: self.n_obs]
 
     def adjoint(self, m: torch.Tensor, wavelets, resid: torch.Tensor, grad: torch.Tensor | None = None):
@@ -415,10 +441,17 @@ class Batch:
         w = self._wavelets(wavelets)
         if grad is None:
             grad = torch.zeros(self.geom.shape, dtype=torch.float32, device=m.device)
+        g = grad
+        if self.graph:
+            m = self._stage("m", m, self.geom.shape)
+            resid = self._stage("resid", resid, (max(self.n_obs, 1),))
+            g = self._stage("grad", None, self.geom.shape).zero_()
         st = _lib.load().fwi_batch_adjoint(self.handle, _dev(m, torch.float32, "m"), w.ctypes.data,
-                                           _dev(resid, torch.float32, "resid"), _dev(grad, torch.float32, "grad"),
+                                           _dev(resid, torch.float32, "resid"), _dev(g, torch.float32, "grad"),
                                            _stream())
         check("fwi_batch_adjoint", st)
+        if g is not grad:
+            grad += g
         return grad
 
     def stats(self) -> dict:

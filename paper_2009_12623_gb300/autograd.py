@@ -48,3 +48,35 @@ def model_velocity(c: torch.Tensor, geom: api.Geometry, wavelet, src, rec: torch
                    atol: float = 0.0) -> torch.Tensor:
     """Differentiable shot record of velocity c (m = 1/c^2, Eq. (1))."""
     return model(1.0 / (c * c), geom, wavelet, src, rec, store, mode, k, atol)
+
+
+class SurveyModeling(torch.autograd.Function):
+    """m (model grid) -> the flat records of every shot of a batch plan
+    (api.Batch): one batched forward sweep keeps all shots' checkpoints in
+    the plan; the backward is one batched reverse sweep, returning
+    sum_s J_s^T dL/dd_s stacked on the model grid.  Each backward must follow
+    its own forward (the plan holds one set of checkpoints)."""
+
+    @staticmethod
+    def forward(ctx, m, plan, wavelets):
+        m = m.detach().contiguous()
+        d = plan.forward(m, wavelets)
+        ctx.save_for_backward(m)
+        ctx.plan, ctx.wavelets = plan, wavelets
+        return d
+
+    @staticmethod
+    def backward(ctx, grad_d):
+        (m,) = ctx.saved_tensors
+        g = ctx.plan.adjoint(m, ctx.wavelets, grad_d.contiguous())
+        return g, None, None
+
+
+def survey(m: torch.Tensor, plan: api.Batch, wavelets) -> torch.Tensor:
+    """Differentiable flat records of all shots of `plan` (split with plan.split)."""
+    return SurveyModeling.apply(m, plan, wavelets)
+
+
+def survey_velocity(c: torch.Tensor, plan: api.Batch, wavelets) -> torch.Tensor:
+    """Differentiable flat records of all shots as a function of velocity c."""
+    return survey(1.0 / (c * c), plan, wavelets)

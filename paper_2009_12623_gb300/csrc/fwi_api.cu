@@ -555,6 +555,7 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
   // the codec reads or writes that buffer.
   CodecStream cs(s);
   if (!cs.ok) return FWI_ERR_CUDA;
+  s = cs.main;  // the sweep's own stream from here on
   auto store_field = [&](const float* f, int j) -> int {
     if (lossy) {
       CK(slot_offset_launch(offs, sizes, j, cs.s));

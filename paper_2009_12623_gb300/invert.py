@@ -34,29 +34,61 @@ def misfit_and_gradient(c: torch.Tensor, shots, d_obs, stores, mode, k, atol):
     return float(total), c.grad.detach()
 
 
-def invert(c0: torch.Tensor, shots, d_obs, iters: int = 10, mode=api.FWI_CKPT_FULL, k: int = 1,
-           atol: float = 1e-4, step: float = 0.02, store_bytes: int = 4 << 30,
-           vmin: float = 1400.0, vmax: float = 6500.0, mask: torch.Tensor | None = None):
+def misfit_and_gradient_batched(c: torch.Tensor, plan: api.Batch, wavelets, d_obs_flat: torch.Tensor):
+    """The same through one batch plan: all shots in one batched forward and
+    one batched reverse sweep (autograd.SurveyModeling)."""
+    c = c.detach().requires_grad_(True)
+    d = autograd.survey_velocity(c, plan, wavelets)
+    r = d - d_obs_flat
+    loss = 0.5 * (r.double() * r.double()).sum()
+    loss.backward()
+    return float(loss.detach()), c.grad.detach()
+
+
+def descend(c0: torch.Tensor, grad_fn, iters: int, step: float, vmin: float, vmax: float,
+            mask: torch.Tensor | None):
     """Steepest descent on velocity.  Every gradient is divided by the size of
     the first iteration's gradient (its largest magnitude), so the first
     update changes the model by at most step x mean velocity and later
-    updates shrink with the gradient; returns (c, misfit history)."""
-    stores = [api.CheckpointStore(store_bytes) for _ in shots]
+    updates shrink with the gradient; returns (c, misfit history, first gradient)."""
     c = c0.clone()
     hist = []
     g0 = None
+    first = None
+    for _ in range(iters):
+        phi, g = grad_fn(c)
+        if mask is not None:
+            g = g * mask
+        if g0 is None:
+            g0 = float(g.abs().max())
+            first = g.clone()
+        hist.append(phi)
+        c = (c - step * float(c0.mean()) * g / g0).clamp(vmin, vmax)
+    return c, hist, first
+
+
+def invert(c0: torch.Tensor, shots, d_obs, iters: int = 10, mode=api.FWI_CKPT_FULL, k: int = 1,
+           atol: float = 1e-4, step: float = 0.02, store_bytes: int = 16 << 30,
+           vmin: float = 1400.0, vmax: float = 6500.0, mask: torch.Tensor | None = None):
+    """Steepest descent with one checkpointed gradient call per shot; each
+    shot's backward runs right after its forward, so one store serves them
+    all.  Returns (c, misfit history)."""
+    store = api.CheckpointStore(store_bytes)
+    stores = [store] * len(shots)
     try:
-        for _ in range(iters):
-            phi, g = misfit_and_gradient(c, shots, d_obs, stores, mode, k, atol)
-            if mask is not None:
-                g = g * mask
-            if g0 is None:
-                g0 = float(g.abs().max())
-            hist.append(phi)
-            c = (c - step * float(c0.mean()) * g / g0).clamp(vmin, vmax)
+        c, hist, _ = descend(c0, lambda cc: misfit_and_gradient(cc, shots, d_obs, stores, mode, k, atol),
+                             iters, step, vmin, vmax, mask)
     finally:
-        for st in stores:
-            st.close()
+        store.close()
+    return c, hist
+
+
+def invert_batched(c0: torch.Tensor, plan: api.Batch, wavelets, d_obs_flat: torch.Tensor, iters: int = 10,
+                   step: float = 0.02, vmin: float = 1400.0, vmax: float = 6500.0,
+                   mask: torch.Tensor | None = None):
+    """Steepest descent through a batch plan (all shots per launch)."""
+    c, hist, _ = descend(c0, lambda cc: misfit_and_gradient_batched(cc, plan, wavelets, d_obs_flat),
+                         iters, step, vmin, vmax, mask)
     return c, hist
 
 
@@ -69,6 +101,7 @@ def _main():
     p.add_argument("--f", type=float, default=10.0)
     p.add_argument("--iters", type=int, default=10)
     p.add_argument("--atol", type=float, default=1e-4)
+    p.add_argument("--per-shot", action="store_true", help="one gradient call per shot instead of a batch plan")
     a = p.parse_args()
     nx, ny, nz = (int(v) for v in a.grid.split(","))
     dev = torch.device("cuda")
@@ -95,12 +128,20 @@ def _main():
     interior = torch.zeros_like(c0)
     interior[nbl:nz - nbl, nbl:ny - nbl, nbl:nx - nbl] = 1.0
     t0 = time.time()
-    c, hist = invert(c0, shots, d_obs, iters=a.iters, atol=a.atol, mask=interior)
+    if a.per_shot:
+        c, hist = invert(c0, shots, d_obs, iters=a.iters, atol=a.atol, mask=interior)
+    else:
+        specs = [api.ShotSpec(0, 0, 0, nx, ny, nz, nt, s, rec.cpu().numpy()) for s in srcs]
+        with api.Batch(geom, specs, mode=api.FWI_CKPT_FULL, atol=a.atol, arena_bytes=64 << 30,
+                       graph=True, tune=True) as plan:
+            c, hist = invert_batched(c0, plan, [w] * len(srcs), plan.concat(d_obs), iters=a.iters,
+                                     mask=interior)
     torch.cuda.synchronize()
     err0 = float(torch.linalg.vector_norm(c0 - torch.from_numpy(v_true).to(dev)))
     err = float(torch.linalg.vector_norm(c - torch.from_numpy(v_true).to(dev)))
     print(json.dumps({"misfit": hist, "model_error_start": err0, "model_error_end": err,
-                      "seconds": time.time() - t0, "nt": nt, "shots": a.shots}))
+                      "seconds": time.time() - t0, "nt": nt, "shots": a.shots,
+                      "path": "per-shot" if a.per_shot else "batch plan"}))
 
 
 if __name__ == "__main__":

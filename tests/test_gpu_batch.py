@@ -152,3 +152,48 @@ def test_batch_errors(cuda):
     with api.Batch(sv.geom, sv.shots, mode=2, k=4, atol=0.0, arena_bytes=1 << 28) as b:
         with pytest.raises(api.FwiError):
             b.adjoint(m, w, b.concat(d_obs))
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_survey_autograd_equals_batch_gradient(cuda, graph):
+    """Autograd over the batch plan (one batched forward, one batched reverse
+    sweep) gives the fused stacked gradient bit for bit."""
+    from paper_2009_12623_gb300 import api, autograd
+    sv = _survey(seed=8)
+    m, w, d_obs = _setup(cuda, sv)
+    with api.Batch(sv.geom, sv.shots, mode=2, k=4, atol=1e-4, arena_bytes=1 << 29, graph=graph) as b:
+        obs = b.concat(d_obs)
+        g_ref, phi = b.gradient(m, w, obs)
+        for _ in range(2):  # the second pass replays the captured graphs
+            mm = m.clone().requires_grad_(True)
+            d = autograd.survey(mm, b, w)
+            loss = 0.5 * ((d - obs).double() ** 2).sum()
+            loss.backward()
+            assert torch.equal(mm.grad, g_ref)
+            assert float(loss) == pytest.approx(phi.sum(), rel=1e-12)
+
+
+def test_batched_inversion_tracks_per_shot_inversion(cuda):
+    """Steepest descent through the batch plan and through one call per shot
+    (full-grid apertures): same first gradient up to FP32 summation order,
+    same misfit history."""
+    from paper_2009_12623_gb300 import api, invert, synth
+    from paper_2009_12623_gb300.api import ShotSpec
+    base = _survey(seed=9, nshots=1)
+    g = base.geom
+    rec = np.array([(i, j, 8) for i in range(6, g.nx - 6, 4) for j in range(6, g.ny - 6, 6)], np.int32)
+    nt = 40
+    geom = api.Geometry(nx=g.nx, ny=g.ny, nz=g.nz, h=g.h, dt=g.dt, nt=nt, nbl=g.nbl, vmax=g.vmax)
+    srcs = [(14, 12, 8), (40, 30, 8), (28, 20, 8)]
+    w = synth.wavelet(nt, g.dt, 25.0)
+    mt = torch.from_numpy(synth.slowness2(base.v_true)).to(cuda)
+    rt = torch.from_numpy(rec).to(cuda)
+    d_obs = [api.forward(geom, mt, w, s, rt) for s in srcs]
+    c0 = torch.from_numpy(base.v0).to(cuda)
+    shots = [(geom, w, s, rt) for s in srcs]
+    c1, h1 = invert.invert(c0, shots, d_obs, iters=3, atol=1e-4, step=0.01, store_bytes=1 << 27)
+    specs = [ShotSpec(0, 0, 0, g.nx, g.ny, g.nz, nt, s, rec) for s in srcs]
+    with api.Batch(geom, specs, mode=1, atol=1e-4, arena_bytes=1 << 28) as plan:
+        c2, h2 = invert.invert_batched(c0, plan, [w] * 3, plan.concat(d_obs), iters=3, step=0.01)
+    assert np.allclose(h1, h2, rtol=1e-5), (h1, h2)
+    assert float(torch.linalg.vector_norm(c1 - c2)) <= 1e-4 * float(torch.linalg.vector_norm(c1 - c0))
