@@ -413,7 +413,9 @@ FZ_HD bool decode_planes_mem(R& rd, int minexp, K& sink, int& emax, int& planes)
       const uint64_t t = rd.peek();
       rd.pos += 1;
       if (!(t & 1ull)) break;
-      const uint64_t pk = rd.peek();
+      // the 63 bits after the group bit usually hold the run's 1; else peek again
+      uint64_t pk = t >> 1;
+      if (!pk) pk = rd.peek();
       const int j = pk ? ctz64(pk) : 64;
       if (j >= 64 - n || rd.pos + j + 1 > rd.end) return false;
       rd.pos += j + 1;
