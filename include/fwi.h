@@ -170,8 +170,11 @@ int fwi_adjoint_store(const fwi_geometry* g, const float* d_m, const float* h_wa
 
 /* The same gradient with every array in host memory (h_m, h_rec_ijk, h_obs,
  * h_grad: same layouts as above; pinned memory gives the fastest copies).
- * Copies inputs to the device, runs fwi_gradient, copies h_grad back
- * (h_grad += ...).  Synchronises. */
+ * Copies the model and receivers, runs the forward sweep while h_obs and
+ * h_grad travel to the device on a second stream, then the misfit and the
+ * reverse sweep (the same kernels as fwi_gradient, bitwise the same result),
+ * and copies h_grad back (h_grad += ...).  h_misfit is required.
+ * Synchronises. */
 int fwi_gradient_host(const fwi_geometry* g, const float* h_m, const float* h_wavelet,
                       int src_i, int src_j, int src_k, const int* h_rec_ijk, int nrec,
                       const float* h_obs, float* h_grad, double* h_misfit, fwi_ckpt_store* st,

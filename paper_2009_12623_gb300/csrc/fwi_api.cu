@@ -825,31 +825,59 @@ int fwi_gradient_host(const fwi_geometry* g, const float* h_m, const float* h_wa
                       int src_j, int src_k, const int* h_rec_ijk, int nrec, const float* h_obs,
                       float* h_grad, double* h_misfit, fwi_ckpt_store* st,
                       const fwi_ckpt_policy* pol, void* stream) {
-  if (!geometry_ok(g) || !h_m || !h_grad || nrec < 0 || (nrec > 0 && (!h_rec_ijk || !h_obs)))
+  if (!geometry_ok(g) || !h_m || !h_grad || !h_misfit || nrec < 0 || (nrec > 0 && (!h_rec_ijk || !h_obs)))
     return FWI_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t C = (size_t)g->nx * g->ny * g->nz;
   const size_t nobs = (size_t)g->nt * nrec;
-  float *dm = nullptr, *dobs = nullptr, *dgrad = nullptr;
+  float *dm = nullptr, *dobs = nullptr, *dgrad = nullptr, *drecs = nullptr;
   int* drec = nullptr;
+  double* dphi = nullptr;
+  double* dpart = nullptr;
+  cudaStream_t cp = nullptr;
+  cudaEvent_t ready = nullptr;
   int rc = FWI_OK;
   if (cudaMallocAsync(&dm, C * 4, s) != cudaSuccess || cudaMallocAsync(&dgrad, C * 4, s) != cudaSuccess ||
       cudaMallocAsync(&dobs, (nobs ? nobs : 1) * 4, s) != cudaSuccess ||
-      cudaMallocAsync(&drec, (nrec ? nrec : 1) * 12, s) != cudaSuccess) {
+      cudaMallocAsync(&drecs, (nobs ? nobs : 1) * 4, s) != cudaSuccess ||
+      cudaMallocAsync(&drec, (nrec ? nrec : 1) * 12, s) != cudaSuccess ||
+      cudaMallocAsync(&dphi, sizeof(double), s) != cudaSuccess ||
+      cudaMallocAsync(&dpart, reduce_scratch_doubles() * sizeof(double), s) != cudaSuccess) {
     cudaGetLastError();
     rc = FWI_ERR_NOMEM;
   }
-  if (!rc && (cudaMemcpyAsync(dm, h_m, C * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-              cudaMemcpyAsync(dgrad, h_grad, C * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-              (nobs && cudaMemcpyAsync(dobs, h_obs, nobs * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
-              (nrec && cudaMemcpyAsync(drec, h_rec_ijk, (size_t)nrec * 12, cudaMemcpyHostToDevice, s) != cudaSuccess)))
+  // the model and receivers are needed first; the observed data and the
+  // incoming gradient only after the forward sweep, so they travel on a
+  // copy stream while it runs
+  if (!rc && (cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking) != cudaSuccess ||
+              cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+              cudaEventRecord(ready, s) != cudaSuccess || cudaStreamWaitEvent(cp, ready, 0) != cudaSuccess))
     rc = FWI_ERR_CUDA;
-  if (!rc) rc = fwi_gradient(g, dm, h_wavelet, src_i, src_j, src_k, drec, nrec, dobs, dgrad, h_misfit,
-                             st, pol, stream);
+  if (!rc && (cudaMemcpyAsync(dm, h_m, C * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+              (nrec && cudaMemcpyAsync(drec, h_rec_ijk, (size_t)nrec * 12, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+              cudaMemsetAsync(dphi, 0, sizeof(double), s) != cudaSuccess ||
+              cudaMemcpyAsync(dgrad, h_grad, C * 4, cudaMemcpyHostToDevice, cp) != cudaSuccess ||
+              (nobs && cudaMemcpyAsync(dobs, h_obs, nobs * 4, cudaMemcpyHostToDevice, cp) != cudaSuccess) ||
+              cudaEventRecord(ready, cp) != cudaSuccess))
+    rc = FWI_ERR_CUDA;
+  if (!rc) rc = fwi_forward_store(g, dm, h_wavelet, src_i, src_j, src_k, drec, nrec, drecs, st, pol, stream);
+  double phi = 0.0;
+  if (!rc && (cudaStreamWaitEvent(s, ready, 0) != cudaSuccess ||
+              misfit_launch(drecs, dobs, nobs, drecs, dphi, dpart, s) != cudaSuccess ||
+              cudaMemcpyAsync(&phi, dphi, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess))
+    rc = FWI_ERR_CUDA;
+  if (!rc) rc = fwi_adjoint_store(g, dm, h_wavelet, src_i, src_j, src_k, drec, nrec, drecs, dgrad, st, pol,
+                                  stream);
   if (!rc && (cudaMemcpyAsync(h_grad, dgrad, C * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
               cudaStreamSynchronize(s) != cudaSuccess))
     rc = FWI_ERR_CUDA;
-  for (void* p : {(void*)dm, (void*)dobs, (void*)dgrad, (void*)drec})
+  if (!rc) *h_misfit = phi;
+  if (cp) {
+    cudaStreamSynchronize(cp);
+    cudaStreamDestroy(cp);
+  }
+  if (ready) cudaEventDestroy(ready);
+  for (void* p : {(void*)dm, (void*)dobs, (void*)dgrad, (void*)drec, (void*)drecs, (void*)dphi, (void*)dpart})
     if (p) cudaFreeAsync(p, s);
   cudaStreamSynchronize(s);
   cudaGetLastError();

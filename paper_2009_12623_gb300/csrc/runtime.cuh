@@ -45,7 +45,7 @@ struct Pool {
 // placed first when SMs free up) and the codec at the lowest priority;
 // 2 = the codec stream at the highest priority.
 #ifndef FWI_PRIO_MODE
-#define FWI_PRIO_MODE 1
+#define FWI_PRIO_MODE 0
 #endif
 
 // A second stream for codec work with a few events, and the stream the

@@ -229,13 +229,17 @@ def test_capacity_overflow_reported(cuda, two_layer):
     assert float(grad.abs().max()) == 0.0
 
 
-def test_gradient_host_equals_device(cuda, two_layer):
+@pytest.mark.parametrize("mode,k", [(1, 1), (2, 10), (3, 4)])
+def test_gradient_host_equals_device(cuda, two_layer, mode, k):
+    """The host-memory entry point (uploads overlapped with the forward sweep,
+    then misfit and reverse sweep) gives the device call's bits."""
     from paper_2009_12623_gb300 import api, synth
     shot, d_obs = two_layer
-    g_dev, phi_dev, _ = _grad(cuda, shot, d_obs, 2, k=10, atol=1e-4)
+    g_dev, phi_dev, _ = _grad(cuda, shot, d_obs, mode, k=k, atol=1e-4)
     with api.CheckpointStore(1 << 30) as st:
         g_host, phi_host = api.gradient_host(shot.geom, synth.slowness2(shot.v0), shot.wavelet, shot.src,
-                                             shot.rec, d_obs.astype(np.float32), st, mode=2, k=10, atol=1e-4)
+                                             shot.rec, d_obs.astype(np.float32), st, mode=mode, k=k,
+                                             atol=1e-4)
     assert np.array_equal(g_host, g_dev) and phi_host == phi_dev
 
 
