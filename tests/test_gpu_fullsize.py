@@ -1,0 +1,123 @@
+"""Parity at the full workload sizes, in the launch configurations the
+benchmark times (same kernels, same tiling and chunking):
+
+* the 881 x 881 x 287 Overthrust-shaped grid: three forward steps from a
+  random smooth state that makes every cell (absorbing layer included)
+  active, against the FP64 oracle over the whole field; a propagated
+  wavefield compressed at atol = 1e-4, bitwise against the oracle's stream;
+  every-K raw checkpoints bitwise equal to full history, and the lossy
+  gradient close to the raw one (properties that hold at any size);
+* the 512^3 codec benchmark snapshot (Sec. 4.2's direct-compression
+  experiment): stream bitwise against the oracle at atol = 1e-4, and the
+  error bound for the whole atol sweep.
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _smooth_state(shape, seed):
+    """Sum of three separable sine modes (float32), amplitude O(1e-3)."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    out = np.zeros(shape, np.float32)
+    for _ in range(3):
+        kx, ky, kz = rng.uniform(0.05, 0.6, 3)
+        px, py, pz = rng.uniform(0, 2 * np.pi, 3)
+        a = np.float32(rng.uniform(0.5, 1.0) * 1e-3)
+        sx = np.sin(kx * np.arange(nx) + px).astype(np.float32)
+        sy = np.sin(ky * np.arange(ny) + py).astype(np.float32)
+        sz = np.sin(kz * np.arange(nz) + pz).astype(np.float32)
+        for z0 in range(0, nz, 32):
+            out[z0:z0 + 32] += a * sz[z0:z0 + 32, None, None] * (sy[:, None] * sx[None, :])[None]
+    return out
+
+
+@pytest.fixture(scope="module")
+def overthrust(cuda):
+    from paper_2009_12623_gb300 import synth
+    shot = synth.overthrust_like_shot(nt=3)
+    return shot
+
+
+def test_fullsize_forward_matches_oracle(cuda, oracle, overthrust):
+    from paper_2009_12623_gb300 import api, synth
+    shot = overthrust
+    g = shot.geom
+    m = synth.slowness2(shot.v0)
+    up = _smooth_state(g.shape, 1)
+    uc = _smooth_state(g.shape, 2)
+    rec = shot.rec[::97]
+    d, _, ul = api.forward(g, torch.from_numpy(m).to(cuda), shot.wavelet, shot.src,
+                           torch.from_numpy(np.ascontiguousarray(rec)).to(cuda),
+                           u_prev_init=torch.from_numpy(up).to(cuda), u_cur_init=torch.from_numpy(uc).to(cuda),
+                           return_state=True)
+    ul = ul.cpu().numpy()
+    d = d.cpu().numpy()
+    og = oracle.geometry(g.nx, g.ny, g.nz, g.h, g.dt, g.nt, g.nbl, g.sponge_R, g.vmax)
+    d_ref, _, ul_ref = oracle.forward(og, m.astype(np.float64), shot.wavelet.astype(np.float64), shot.src, rec,
+                                      u_prev_init=up.astype(np.float64), u_cur_init=uc.astype(np.float64),
+                                      return_state=True)
+    err = np.linalg.norm(ul.astype(np.float64) - ul_ref) / np.linalg.norm(ul_ref)
+    assert err < 1e-5, err
+    assert np.linalg.norm(d - d_ref) / np.linalg.norm(d_ref) < 1e-5
+
+
+def test_fullsize_codec_stream_bitexact(cuda, oracle, overthrust):
+    from paper_2009_12623_gb300 import api, synth
+    shot = overthrust
+    g = api.Geometry(**{**shot.geom.__dict__, "nt": 400})
+    rec = torch.from_numpy(np.ascontiguousarray(shot.rec[:1])).to(cuda)
+    _, _, ul = api.forward(g, torch.from_numpy(synth.slowness2(shot.v0)).to(cuda), synth.wavelet(400, g.dt, 8.0),
+                           shot.src, rec, return_state=True)
+    s = api.zfp_compress(ul, 1e-4)
+    ref = oracle.zfp_compress(ul.cpu().numpy(), 1e-4)
+    assert s.cpu().numpy().tobytes() == ref
+    dec = api.zfp_decompress(s.clone(), ul.shape)
+    assert float((dec - ul).abs().max()) <= 1e-4
+
+
+def test_fullsize_every_k_raw_equals_full_history(cuda, overthrust):
+    from paper_2009_12623_gb300 import api, synth
+    shot = overthrust
+    g = api.Geometry(**{**shot.geom.__dict__, "nt": 40})
+    m = torch.from_numpy(synth.slowness2(shot.v0)).to(cuda)
+    rec = torch.from_numpy(np.ascontiguousarray(shot.rec)).to(cuda)
+    w = synth.wavelet(40, g.dt, 8.0)
+    d_obs = torch.zeros((40, len(shot.rec)), device=cuda)
+    with api.CheckpointStore(40 << 30) as st:
+        g_full, p_full = api.gradient(g, m, w, shot.src, rec, d_obs, st, mode=1)
+        g_k, p_k = api.gradient(g, m, w, shot.src, rec, d_obs, st, mode=2, k=7)
+    assert torch.equal(g_full, g_k) and p_full == p_k
+    assert float(g_full.abs().max()) > 0
+
+
+def test_fullsize_lossy_gradient_close_to_raw(cuda, overthrust):
+    from paper_2009_12623_gb300 import api, synth
+    shot = overthrust
+    nt = 150
+    g = api.Geometry(**{**shot.geom.__dict__, "nt": nt})
+    m = torch.from_numpy(synth.slowness2(shot.v0)).to(cuda)
+    rec = torch.from_numpy(np.ascontiguousarray(shot.rec)).to(cuda)
+    w = synth.wavelet(nt, g.dt, 8.0)
+    d_obs = api.forward(g, torch.from_numpy(synth.slowness2(shot.v_true)).to(cuda), w, shot.src, rec)
+    with api.CheckpointStore(40 << 30) as st:
+        g_raw, _ = api.gradient(g, m, w, shot.src, rec, d_obs, st, mode=2, k=30)
+        g_lossy, _ = api.gradient(g, m, w, shot.src, rec, d_obs, st, mode=1, atol=1e-4)
+    num = api.dot_f64(g_lossy - g_raw, g_lossy - g_raw)
+    den = api.dot_f64(g_raw, g_raw)
+    assert den > 0 and (num / den) ** 0.5 < 1e-4
+
+
+def test_codec_benchmark_512_bitexact_and_bounded(cuda, oracle):
+    from paper_2009_12623_gb300 import api, synth
+    f = synth.shells_field(512, seed=0)
+    t = torch.from_numpy(f).to(cuda)
+    s = api.zfp_compress(t, 1e-4)
+    assert s.cpu().numpy().tobytes() == oracle.zfp_compress(f, 1e-4)
+    for atol in (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+        s = api.zfp_compress(t, atol)
+        dec = api.zfp_decompress(s.clone(), f.shape)
+        assert float((dec - t).abs().max()) <= atol, atol
