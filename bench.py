@@ -46,9 +46,10 @@ def parse():
     p.add_argument("--no-verify", action="store_true")
     p.add_argument("--arena-gb", type=float, default=0.0,
                    help="checkpoint arena size (0 = all free memory minus the working set)")
-    p.add_argument("--workload", default="overthrust", choices=["overthrust", "batch", "fwi"],
+    p.add_argument("--workload", default="overthrust", choices=["overthrust", "batch", "fwi", "codec"],
                    help="batch: 32-shot survey, batched plan against one call per shot; "
-                        "fwi: 16-shot inversion through autograd, batched against per shot")
+                        "fwi: 16-shot inversion through autograd, batched against per shot; "
+                        "codec: 512^3 shell snapshots, atol sweep")
     p.add_argument("--iters", type=int, default=10, help="fwi workload: descent iterations per path")
     p.add_argument("--shots", type=int, default=32)
     p.add_argument("--ckpt-k", type=int, default=10, help="batch workload: checkpoint pair every K steps")
@@ -680,6 +681,73 @@ def run_fwi_inversion(args):
     print(json.dumps(line), flush=True)
 
 
+def run_codec(args):
+    """Codec microbenchmark: 512^3 FP32 snapshots (seeded sums of 8 spherical
+    Ricker shells plus 1e-7 noise), compress + decompress at atol in
+    {1e-1 .. 1e-6}: compression factor, max error, PSNR and GB/s (uncompressed
+    bytes / kernel time, CUDA events).  value = compress GB/s at atol = 1e-4."""
+    import numpy as np
+    import torch
+    ws, rank, local, pg = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_12623_gb300 import api, synth
+    n = 512
+    fields = [torch.from_numpy(synth.shells_field(n, seed=s)).to(dev) for s in range(max(1, args.steps))]
+    nbytes = n ** 3 * 4
+    out = torch.empty(api.zfp_max_compressed_bytes(n, n, n), dtype=torch.uint8, device=dev)
+    dec = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    pk, peak_kind = peaks()
+    rows = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for atol in (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+        for f in fields:  # warm-up
+            s = api.zfp_compress(f, atol, out=out)
+            api.zfp_decompress(s, f.shape, out=dec)
+        torch.cuda.synchronize()
+        api.profile_reset()
+        api.profile_enable(True)
+        cf, err, psnr = [], 0.0, []
+        for f in fields:
+            for _ in range(max(1, args.warmup)):
+                s = api.zfp_compress(f, atol, out=out)
+                api.zfp_decompress(s, f.shape, out=dec)
+            torch.cuda.synchronize()
+            cf.append(nbytes / s.numel())
+            d = (dec - f).abs()
+            err = max(err, float(d.max()))
+            rng = float(f.max() - f.min())
+            mse = float((d.double() ** 2).mean())
+            psnr.append(20 * np.log10(rng) - 10 * np.log10(mse) if mse > 0 else float("inf"))
+        api.profile_enable(False)
+        prof = api.profile_read()
+        e_ms, e_n = prof["zfp_encode"]
+        d_ms, d_n = prof["zfp_decode"]
+        enc = nbytes / (e_ms / e_n / 1e3) / 1e9
+        dcd = nbytes / (d_ms / d_n / 1e3) / 1e9
+        rows.append({"atol": atol, "compression_factor": float(np.mean(cf)), "max_error": err,
+                     "max_error_below_atol": err <= atol, "psnr_db": float(np.mean(psnr)),
+                     "compress_GBps": enc, "decompress_GBps": dcd,
+                     "compress_frac_of_hbm": (nbytes + nbytes / np.mean(cf)) / (e_ms / e_n / 1e3) / 1e9 / pk["hbm_gbs"],
+                     "decompress_frac_of_hbm": (nbytes + nbytes / np.mean(cf)) / (d_ms / d_n / 1e3) / 1e9 / pk["hbm_gbs"]})
+    clk = clocks.stop()
+    r4 = [r for r in rows if r["atol"] == 1e-4][0]
+    line = {"metric": "codec compress GB/s (uncompressed bytes / kernel time)", "value": r4["compress_GBps"],
+            "unit": "GB/s", "n_gpus": ws, "steps": len(fields), "warmup": 1, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"codec microbenchmark: {n}^3 FP32 shell snapshots (8 spherical 15 Hz Ricker shells, "
+                                   f"radii 50-200 cells, N(0,1) amplitudes, 1e-7 noise), seeds 0..{len(fields) - 1}",
+                       "l2_flush": "inputs larger than L2 (512 MB fields)"},
+            "sweep": rows, "peak": {"hbm_gbs": pk["hbm_gbs"], "source": peak_kind}, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -688,6 +756,8 @@ def main():
         run_batch(args)
     elif args.workload == "fwi":
         run_fwi_inversion(args)
+    elif args.workload == "codec":
+        run_codec(args)
     else:
         run_fwi(args)
 
