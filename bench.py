@@ -46,10 +46,11 @@ def parse():
     p.add_argument("--no-verify", action="store_true")
     p.add_argument("--arena-gb", type=float, default=0.0,
                    help="checkpoint arena size (0 = all free memory minus the working set)")
-    p.add_argument("--workload", default="overthrust", choices=["overthrust", "batch", "fwi", "codec"],
+    p.add_argument("--workload", default="overthrust", choices=["overthrust", "batch", "fwi", "codec", "tradeoff"],
                    help="batch: 32-shot survey, batched plan against one call per shot; "
                         "fwi: 16-shot inversion through autograd, batched against per shot; "
-                        "codec: 512^3 shell snapshots, atol sweep")
+                        "codec: 512^3 shell snapshots, atol sweep; "
+                        "tradeoff: gradient error vs memory for compression, subsampling, binomial")
     p.add_argument("--iters", type=int, default=10, help="fwi workload: descent iterations per path")
     p.add_argument("--shots", type=int, default=32)
     p.add_argument("--ckpt-k", type=int, default=10, help="batch workload: checkpoint pair every K steps")
@@ -748,6 +749,91 @@ def run_codec(args):
         print(json.dumps(line), flush=True)
 
 
+def run_tradeoff(args):
+    """Memory / error / time trade-off of the checkpointing options on an
+    Overthrust-shaped shot (440 x 440 x 200 at 25 m, 1200 steps of 1.75 ms,
+    8 Hz): every gradient against the exact one from raw checkpoint pairs
+    every 40 steps -- full-history lossy compression over atol (Sec. 4.4),
+    subsampling of the imaging condition over f (Sec. 4.7), binomial
+    checkpointing over the number of snapshot pairs (raw and compressed).
+    Memory reduction = bytes of full raw history / bytes held; error = relative
+    L2 and angle of the gradient (FP64 reductions on the GPU)."""
+    import numpy as np
+    import torch
+    ws, rank, local, pg = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_12623_gb300 import api, synth
+
+    shot = synth.overthrust_like_shot(nx=440, ny=440, nz=200, nt=1200, nbl=40, rec_stride=2)
+    g = shot.geom
+    m0 = torch.from_numpy(synth.slowness2(shot.v0)).to(dev)
+    rec = torch.from_numpy(shot.rec).to(dev)
+    w = shot.wavelet
+    d_obs = api.forward(g, torch.from_numpy(synth.slowness2(shot.v_true)).to(dev), w, shot.src, rec)
+    cells = g.nx * g.ny * g.nz
+    full_raw = g.nt * cells * 4
+    store = api.CheckpointStore(128 << 30)  # subsampling at f = 2 holds 600 raw states (93 GB)
+
+    def grad(mode, k=1, atol=0.0):
+        out = torch.zeros(g.shape, dtype=torch.float32, device=dev)
+        api.gradient(g, m0, w, shot.src, rec, d_obs, store, mode=mode, k=k, atol=atol, grad=out)  # warm-up
+        torch.cuda.synchronize()
+        out.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        api.gradient(g, m0, w, shot.src, rec, d_obs, store, mode=mode, k=k, atol=atol, grad=out)
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1), store.stats()
+
+    ref, t_ref, _ = grad(api.FWI_CKPT_EVERY_K, 40)
+    rr = api.dot_f64(ref, ref)
+
+    def err(gr):
+        d = gr - ref
+        cos = api.dot_f64(gr, ref) / np.sqrt(api.dot_f64(gr, gr) * rr)
+        return float(np.sqrt(api.dot_f64(d, d) / rr)), float(np.arccos(min(1.0, max(-1.0, cos))))
+
+    def forward_steps(mode, k):
+        return sum(1 for a in api.ckpt_schedule(g.nt, mode, k) if a[0] in (1, 4))
+
+    rows = {"compression": [], "subsampling": [], "binomial": []}
+    for atol in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+        gr, ms, st = grad(api.FWI_CKPT_FULL, 1, atol)
+        e, ang = err(gr)
+        rows["compression"].append({"atol": atol, "memory_reduction": full_raw / st["used_bytes"],
+                                    "held_GiB": st["used_bytes"] / 2**30, "rel_l2": e, "angle_rad": ang, "ms": ms})
+    for f in (2, 4, 8, 16, 32):
+        gr, ms, st = grad(api.FWI_CKPT_SUBSAMPLE, f)
+        e, ang = err(gr)
+        rows["subsampling"].append({"f": f, "memory_reduction": full_raw / max(1, st["used_bytes"]),
+                                    "held_GiB": st["used_bytes"] / 2**30, "rel_l2": e, "angle_rad": ang, "ms": ms})
+    for snaps in (4, 8, 16, 32, 64):
+        for atol in (0.0, 1e-4):
+            gr, ms, st = grad(api.FWI_CKPT_BINOMIAL, snaps, atol)
+            e, ang = err(gr)
+            rows["binomial"].append({"snapshot_pairs": snaps, "atol": atol,
+                                     "forward_steps": forward_steps(api.FWI_CKPT_BINOMIAL, snaps),
+                                     "memory_reduction": full_raw / max(1, st["used_bytes"]),
+                                     "held_GiB": st["used_bytes"] / 2**30, "rel_l2": e, "angle_rad": ang, "ms": ms})
+    store.close()
+    line = {"metric": "gradient error vs checkpoint memory (compression, subsampling, binomial)",
+            "value": None, "unit": None, "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": None,
+            "higher_is_better": None, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"overthrust-like single shot {g.nx}x{g.ny}x{g.nz} at {g.h:.0f} m, nt={g.nt} "
+                                   f"(dt={g.dt * 1e3:.2f} ms), 8 Hz, {len(shot.rec)} receivers; reference: raw "
+                                   f"checkpoint pairs every 40 steps ({t_ref:.0f} ms)",
+                       "full_raw_history_GiB": full_raw / 2**30},
+            "tradeoff": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -758,6 +844,8 @@ def main():
         run_fwi_inversion(args)
     elif args.workload == "codec":
         run_codec(args)
+    elif args.workload == "tradeoff":
+        run_tradeoff(args)
     else:
         run_fwi(args)
 
