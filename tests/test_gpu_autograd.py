@@ -125,3 +125,36 @@ def test_short_inversion_reduces_misfit(cuda):
     c0 = _t(cuda, base.v0)
     c, hist = invert.invert(c0, shots, d_obs, iters=4, atol=1e-5, step=0.01, store_bytes=1 << 28)
     assert hist[-1] < hist[0], hist
+
+
+def test_gradient_angle_vs_fp64_oracle_across_atol(cuda, oracle):
+    """The angle between the autograd gradient with compressed checkpoints
+    and the uncompressed FP64 oracle gradient (Sec. 4.4's gradient-angle
+    experiment) on a reduced version of the differentiable-FWI case (layered
+    model with +-8% anomalies, smoothed start): it shrinks as atol tightens
+    and stays small at every tolerance."""
+    from paper_2009_12623_gb300 import api, autograd, synth
+    nx, ny, nz, nbl, nt = 48, 44, 36, 8, 220
+    v = synth.layered_velocity(nx, ny, nz, seed=1, water=nbl + 3, vmax=3000.0, nlayers=6, fault_shift=4)
+    vt = synth.add_anomalies(v, seed=2, amplitude=0.08)
+    v0 = synth.smooth(vt, 2.0)
+    g = api.Geometry(nx=nx, ny=ny, nz=nz, h=10.0, dt=1e-3, nt=nt, nbl=nbl, vmax=float(vt.max()))
+    w = synth.wavelet(nt, g.dt, 20.0)
+    src = (nx // 2, ny // 2, nbl + 2)
+    rec = np.array([(i, j, nbl + 2) for i in range(nbl, nx - nbl, 2) for j in range(nbl, ny - nbl, 4)], np.int32)
+    og = oracle.geometry(nx, ny, nz, g.h, g.dt, nt, nbl, g.sponge_R, g.vmax)
+    d_obs = oracle.forward(og, synth.slowness2(vt).astype(np.float64), w.astype(np.float64), src, rec)
+    g_ref, *_ = oracle.gradient(og, synth.slowness2(v0).astype(np.float64), w.astype(np.float64), src, rec, d_obs)
+    obs = _t(cuda, d_obs.astype(np.float32))
+    angles = {}
+    for atol in (1e-2, 1e-4, 1e-6):
+        mm = _t(cuda, synth.slowness2(v0)).requires_grad_(True)
+        with api.CheckpointStore(1 << 30) as st:
+            d = autograd.model(mm, g, w, src, _t(cuda, rec), st, mode=api.FWI_CKPT_FULL, atol=atol)
+            (0.5 * ((d - obs).double() ** 2).sum()).backward()
+        gg = mm.grad.cpu().numpy().astype(np.float64)
+        cos = float(np.dot(gg.ravel(), g_ref.ravel()) / (np.linalg.norm(gg) * np.linalg.norm(g_ref)))
+        angles[atol] = float(np.arccos(min(1.0, cos)))
+    print("gradient angle vs FP64 oracle:", angles)
+    assert angles[1e-2] >= angles[1e-4] >= angles[1e-6] * 0.9
+    assert angles[1e-6] < 1e-3 and angles[1e-4] < 1e-3 and angles[1e-2] < 5e-2
