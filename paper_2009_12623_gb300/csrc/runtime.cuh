@@ -39,47 +39,22 @@ struct Pool {
   }
 };
 
-// Scheduling priority of the sweep's two streams: 0 = the caller's stream
-// runs the stencils and a default-priority side stream the codec; 1 = the
-// stencils run on an internal high-priority stream (so their CTAs are
-// placed first when SMs free up) and the codec at the lowest priority;
-// 2 = the codec stream at the highest priority.
-#ifndef FWI_PRIO_MODE
-#define FWI_PRIO_MODE 0
-#endif
-
-// A second stream for codec work with a few events, and the stream the
-// sweep itself runs on (`main`: the caller's stream, or an internal stream
-// forked from it).  On destruction the codec stream is joined into `main`
-// and `main` into the caller's stream, so stream-ordered frees on the
-// caller's stream stay safe on every return path.
+// A second stream for codec work with a few events.  `main` is the stream
+// the sweep itself runs on (the caller's).  On destruction the codec stream
+// is joined into it, so stream-ordered frees on the caller's stream stay
+// safe on every return path.
 struct CodecStream {
   cudaStream_t owner;
-  cudaStream_t main = nullptr;
+  cudaStream_t main;
   cudaStream_t s = nullptr;
   cudaEvent_t ev[8] = {nullptr};
   cudaEvent_t done = nullptr;
-  bool own_main = false;
   bool ok = false;
   explicit CodecStream(cudaStream_t o) : owner(o), main(o) {
-    int least = 0, greatest = 0;
-    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
-      cudaGetLastError();
-      least = greatest = 0;
-    }
-    const int codec_prio = FWI_PRIO_MODE == 1 ? least : FWI_PRIO_MODE == 2 ? greatest : least;
-    if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, codec_prio) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       s = nullptr;
       return;
-    }
-    if (FWI_PRIO_MODE == 1) {
-      if (cudaStreamCreateWithPriority(&main, cudaStreamNonBlocking, greatest) != cudaSuccess) {
-        cudaGetLastError();
-        main = owner;
-        return;
-      }
-      own_main = true;
     }
     for (auto& e : ev)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
@@ -90,9 +65,8 @@ struct CodecStream {
       cudaGetLastError();
       return;
     }
-    // both streams start after everything the owner issued so far
-    ok = cudaEventRecord(done, owner) == cudaSuccess && cudaStreamWaitEvent(s, done, 0) == cudaSuccess &&
-         (!own_main || cudaStreamWaitEvent(main, done, 0) == cudaSuccess);
+    // codec work may only start after everything the owner issued so far
+    ok = cudaEventRecord(done, owner) == cudaSuccess && cudaStreamWaitEvent(s, done, 0) == cudaSuccess;
   }
   // main waits for all codec work issued so far
   cudaError_t join() {
@@ -104,10 +78,6 @@ struct CodecStream {
     if (s) {
       if (done) join();
       cudaStreamDestroy(s);
-    }
-    if (own_main) {
-      if (done && cudaEventRecord(done, main) == cudaSuccess) cudaStreamWaitEvent(owner, done, 0);
-      cudaStreamDestroy(main);
     }
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
