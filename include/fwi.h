@@ -256,6 +256,17 @@ typedef struct {
 } fwi_batch_stats;
 int fwi_batch_get_stats(const fwi_batch* b, fwi_batch_stats* out);
 
+/* ---- failure detection ---------------------------------------------------- */
+/* Every device-side wait of the library (TMA-completion barriers of the
+ * stencil pipeline, look-back spins of the single-pass encoder) is bounded:
+ * when it gives up, the kernel flags a timeout, waits (bounded) for its own
+ * copies in flight and returns, and the call returns FWI_ERR_TIMEOUT with the
+ * context still usable.  This self-test runs that path on purpose: one CTA
+ * waits `polls` polls (1 .. 2^20) on a barrier nothing ever completes.  It
+ * returns FWI_ERR_TIMEOUT when the bounded wait works (FWI_ERR_ARG for a bad
+ * count).  Synchronises. */
+int fwi_selftest_bounded_wait(long long polls, void* stream);
+
 /* ---- fixed-accuracy codec (Sec. 1.4) -------------------------------------- */
 /* Stream format (shared bit-for-bit with the CPU oracle):
  *   64-byte header (magic "FCZ1", version, nx, ny, nz, minexp, nblocks,

@@ -26,7 +26,7 @@ EXPORTS = [
     "fwi_status_string", "fwi_kernel_launch_count", "fwi_profile_enable", "fwi_profile_reset",
     "fwi_profile_read", "zfp_compress_fixed_accuracy_noalloc", "fwi_forward_store",
     "fwi_adjoint_store", "fwi_batch_create", "fwi_batch_destroy", "fwi_batch_gradient",
-    "fwi_batch_forward", "fwi_batch_adjoint", "fwi_batch_get_stats",
+    "fwi_batch_forward", "fwi_batch_adjoint", "fwi_batch_get_stats", "fwi_selftest_bounded_wait",
 ]
 KERNEL_CLASSES = ["stencil_forward", "stencil_adjoint_imaging", "zfp_encode", "zfp_decode", "other"]
 
@@ -122,6 +122,7 @@ def load() -> C.CDLL:
         L.fwi_batch_forward.argtypes = [vp, fp, vp, fp, vp]
         L.fwi_batch_adjoint.argtypes = [vp, fp, vp, fp, fp, vp]
         L.fwi_batch_get_stats.argtypes = [vp, C.POINTER(BatchStats)]
+        L.fwi_selftest_bounded_wait.argtypes = [C.c_longlong, vp]
         _lib = L
         return L
 

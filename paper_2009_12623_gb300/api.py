@@ -496,3 +496,9 @@ def gradient_per_shot(geom: Geometry, m: torch.Tensor, shots: list, wavelets, d_
         grad[s.window] += g
         phis.append(phi)
     return grad, np.array(phis)
+
+
+def selftest_bounded_wait(polls: int = 1000) -> int:
+    """fwi_selftest_bounded_wait: status of a kernel whose bounded wait is made
+    to run out (FWI_ERR_TIMEOUT when the mechanism works)."""
+    return _lib.load().fwi_selftest_bounded_wait(int(polls), _stream())

@@ -183,6 +183,10 @@ cudaError_t gather_multi_launch(int nfields, const RecTask* t, const int* nrec, 
 cudaError_t inject_multi_launch(int nfields, const RecTask* t, const int* nrec, float dt, float weight,
                                 cudaStream_t s);
 
+// Bounded-wait self-test: one CTA waits `polls` polls on an mbarrier that
+// never completes and flags ST_TIMEOUT in *d_status.
+cudaError_t wait_selftest_launch(int* d_status, long polls, cudaStream_t s);
+
 // Residual r = a - b, FP64 half-sum-of-squares added to *d_acc; dot product
 // likewise.  `part` holds reduce_scratch_doubles() doubles; the summation
 // order is fixed, so results are bitwise reproducible.

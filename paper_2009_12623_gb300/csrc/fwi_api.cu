@@ -884,6 +884,27 @@ int fwi_gradient_host(const fwi_geometry* g, const float* h_m, const float* h_wa
   return rc;
 }
 
+int fwi_selftest_bounded_wait(long long polls, void* stream) {
+  if (polls < 1 || polls > (1LL << 20)) return FWI_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d_status = nullptr;
+  if (cudaMallocAsync(&d_status, sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    return FWI_ERR_NOMEM;
+  }
+  int flags = 0;
+  int rc = FWI_OK;
+  if (cudaMemsetAsync(d_status, 0, sizeof(int), s) != cudaSuccess ||
+      wait_selftest_launch(d_status, (long)polls, s) != cudaSuccess ||
+      cudaMemcpyAsync(&flags, d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    rc = FWI_ERR_CUDA;
+  cudaFreeAsync(d_status, s);
+  cudaStreamSynchronize(s);
+  cudaGetLastError();
+  return rc ? rc : status_from_flags(flags);
+}
+
 size_t zfp_max_compressed_bytes(int nx, int ny, int nz) {
   if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
   return zlayout(nx, ny, nz).max_bytes;

@@ -103,3 +103,9 @@ def test_batch_argument_validation_without_gpu(fwi_lib):
     assert create(C.byref(g), 1, shots, None, C.byref(pol), 1 << 20, 8, C.byref(out)) == _lib.FWI_ERR_ARG
     assert fwi_lib.fwi_batch_destroy(None) == _lib.FWI_ERR_ARG
     assert fwi_lib.fwi_batch_get_stats(None, None) == _lib.FWI_ERR_ARG
+
+
+def test_selftest_argument_validation_without_gpu(fwi_lib):
+    from paper_2009_12623_gb300 import _lib
+    assert fwi_lib.fwi_selftest_bounded_wait(0, None) == _lib.FWI_ERR_ARG
+    assert fwi_lib.fwi_selftest_bounded_wait((1 << 20) + 1, None) == _lib.FWI_ERR_ARG

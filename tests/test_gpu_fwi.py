@@ -263,3 +263,16 @@ def test_bad_receiver_rejected(cuda):
     rec[0, 0] = shot.geom.nx + 5
     with pytest.raises(api.FwiError):
         api.forward(shot.geom, _dev(cuda, synth.slowness2(shot.v0)), shot.wavelet, shot.src, _dev(cuda, rec))
+
+
+def test_bounded_wait_times_out_and_context_survives(cuda, two_layer):
+    """A device wait that nothing completes gives up, reports FWI_ERR_TIMEOUT,
+    and the next call on the same context works."""
+    import time
+    from paper_2009_12623_gb300 import _lib, api
+    t0 = time.time()
+    assert api.selftest_bounded_wait(2000) == _lib.FWI_ERR_TIMEOUT
+    assert time.time() - t0 < 30.0
+    shot, d_obs = two_layer
+    g, phi, _ = _grad(cuda, shot, d_obs, 2, k=10)
+    assert np.isfinite(g).all() and phi > 0
