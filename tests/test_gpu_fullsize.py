@@ -5,8 +5,10 @@ benchmark times (same kernels, same tiling and chunking):
   random smooth state that makes every cell (absorbing layer included)
   active, against the FP64 oracle over the whole field; a propagated
   wavefield compressed at atol = 1e-4, bitwise against the oracle's stream;
-  every-K raw checkpoints bitwise equal to full history, and the lossy
-  gradient close to the raw one (properties that hold at any size);
+  a 24-step gradient over the whole grid within 1e-4 of the uncompressed
+  FP64 oracle gradient; every-K raw checkpoints bitwise equal to full
+  history, and the lossy gradient close to the raw one (properties that
+  hold at any size);
 * the 512^3 codec benchmark snapshot (Sec. 4.2's direct-compression
   experiment): stream bitwise against the oracle at atol = 1e-4, and the
   error bound for the whole atol sweep.
@@ -121,3 +123,28 @@ def test_codec_benchmark_512_bitexact_and_bounded(cuda, oracle):
         s = api.zfp_compress(t, atol)
         dec = api.zfp_decompress(s.clone(), f.shape)
         assert float((dec - t).abs().max()) <= atol, atol
+
+
+def test_fullsize_gradient_matches_fp64_oracle(cuda, oracle, overthrust):
+    """The gradient on the full 881 x 881 x 287 grid (24 steps, the benchmark's
+    kernels and tiling over every cell) within 1e-4 relative L2 of the
+    uncompressed FP64 oracle gradient (every-8 raw pairs on the oracle side,
+    full raw history on the GPU)."""
+    from paper_2009_12623_gb300 import api, synth
+    shot = overthrust
+    nt = 24
+    g = api.Geometry(**{**shot.geom.__dict__, "nt": nt})
+    w = synth.wavelet(nt, g.dt, 8.0, t0=0.01)  # the Ricker peak inside the short record
+    rec = np.ascontiguousarray(shot.rec[::7])
+    m = synth.slowness2(shot.v0)
+    og = oracle.geometry(g.nx, g.ny, g.nz, g.h, g.dt, nt, g.nbl, g.sponge_R, g.vmax)
+    d_obs = np.zeros((nt, len(rec)))  # Phi = 1/2 |d_sim|^2: a residual of full size
+    g_ref, phi_ref, *_ = oracle.gradient(og, m.astype(np.float64), w.astype(np.float64), shot.src, rec, d_obs,
+                                         mode=oracle.CKPT_EVERY_K, k=8)
+    with api.CheckpointStore(32 << 30) as st:
+        gg, phi = api.gradient(g, torch.from_numpy(m).to(cuda), w, shot.src, torch.from_numpy(rec).to(cuda),
+                               torch.zeros((nt, len(rec)), device=cuda), st, mode=1)
+    gg = gg.cpu().numpy().astype(np.float64)
+    assert np.abs(g_ref).max() > 0
+    assert np.linalg.norm(gg - g_ref) / np.linalg.norm(g_ref) < 1e-4
+    assert phi == pytest.approx(phi_ref, rel=1e-4)
