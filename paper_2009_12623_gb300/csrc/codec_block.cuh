@@ -142,11 +142,38 @@ FZ_HD void xform_inv(uint32_t* q) {
   for (int l = 0; l < 16; ++l) lift_inv_u(q[4 * l], q[4 * l + 1], q[4 * l + 2], q[4 * l + 3]);
 }
 
+// Byte permute: byte i of the result is byte ((s >> 4i) & 7) of the 8 bytes
+// of (x, y), x first.
+FZ_HD uint32_t byte_perm(uint32_t x, uint32_t y, uint32_t s) {
+#ifdef __CUDA_ARCH__
+  return __byte_perm(x, y, s);
+#else
+  const uint64_t v = (uint64_t)x | ((uint64_t)y << 32);
+  uint32_t r = 0;
+  for (int i = 0; i < 4; ++i) r |= (uint32_t)((v >> (8 * ((s >> (4 * i)) & 7u))) & 0xffu) << (8 * i);
+  return r;
+#endif
+}
+
 // 32x32 bit-matrix transpose in registers: afterwards bit i of a[b] is what
-// was bit b of a[i] (recursive exchange of the off-diagonal blocks).
+// was bit b of a[i] (recursive exchange of the off-diagonal blocks).  The
+// 16-bit and 8-bit exchanges are byte permutes (two per word pair).
 FZ_HD void transpose32(uint32_t* a) {
 #pragma unroll
-  for (int lv = 0; lv < 5; ++lv) {
+  for (int k = 0; k < 16; ++k) {  // halves: a[k].hi <-> a[k+16].lo
+    const uint32_t x = a[k], y = a[k + 16];
+    a[k] = byte_perm(x, y, 0x5410u);
+    a[k + 16] = byte_perm(x, y, 0x7632u);
+  }
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {  // bytes: bytes 1, 3 of a[k] <-> bytes 0, 2 of a[k+8]
+    if (k & 8) continue;
+    const uint32_t x = a[k], y = a[k + 8];
+    a[k] = byte_perm(x, y, 0x6240u);
+    a[k + 8] = byte_perm(x, y, 0x7351u);
+  }
+#pragma unroll
+  for (int lv = 2; lv < 5; ++lv) {
     const int j = 16 >> lv;
     const uint32_t m = lv == 0 ? 0x0000FFFFu : lv == 1 ? 0x00FF00FFu : lv == 2 ? 0x0F0F0F0Fu
                      : lv == 3 ? 0x33333333u : 0x55555555u;
