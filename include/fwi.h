@@ -267,6 +267,17 @@ int fwi_batch_get_stats(const fwi_batch* b, fwi_batch_stats* out);
  * count).  Synchronises. */
 int fwi_selftest_bounded_wait(long long polls, void* stream);
 
+/* Self-test of the damping quotient of the leapfrog kernels (Sec. 2, Eq. (1)
+ * with the absorbing layer: the update is divided by 1 + eta, eta >= 0):
+ * d_out[i] = d_num[i] / d_den[i] computed exactly as the stencil kernels
+ * compute it (reciprocal estimate, one Newton-Raphson step, remainder
+ * correction), so that tests can compare it with IEEE division.  Device
+ * arrays of n floats; d_den[i] must lie in [1, 2^126) and d_num[i] be
+ * finite.  Returns FWI_ERR_ARG for n < 0 or a null pointer with n > 0.
+ * Synchronises. */
+int fwi_selftest_damped_quotient(const float* d_num, const float* d_den, float* d_out, long long n,
+                                 void* stream);
+
 /* ---- fixed-accuracy codec (Sec. 1.4) -------------------------------------- */
 /* Stream format (shared bit-for-bit with the CPU oracle):
  *   64-byte header (magic "FCZ1", version, nx, ny, nz, minexp, nblocks,

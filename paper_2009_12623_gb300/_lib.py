@@ -27,6 +27,7 @@ EXPORTS = [
     "fwi_profile_read", "zfp_compress_fixed_accuracy_noalloc", "fwi_forward_store",
     "fwi_adjoint_store", "fwi_batch_create", "fwi_batch_destroy", "fwi_batch_gradient",
     "fwi_batch_forward", "fwi_batch_adjoint", "fwi_batch_get_stats", "fwi_selftest_bounded_wait",
+    "fwi_selftest_damped_quotient",
 ]
 KERNEL_CLASSES = ["stencil_forward", "stencil_adjoint_imaging", "zfp_encode", "zfp_decode", "other"]
 
@@ -123,6 +124,7 @@ def load() -> C.CDLL:
         L.fwi_batch_adjoint.argtypes = [vp, fp, vp, fp, fp, vp]
         L.fwi_batch_get_stats.argtypes = [vp, C.POINTER(BatchStats)]
         L.fwi_selftest_bounded_wait.argtypes = [C.c_longlong, vp]
+        L.fwi_selftest_damped_quotient.argtypes = [vp, vp, vp, C.c_longlong, vp]
         _lib = L
         return L
 

@@ -502,3 +502,15 @@ def selftest_bounded_wait(polls: int = 1000) -> int:
     """fwi_selftest_bounded_wait: status of a kernel whose bounded wait is made
     to run out (FWI_ERR_TIMEOUT when the mechanism works)."""
     return _lib.load().fwi_selftest_bounded_wait(int(polls), _stream())
+
+
+def selftest_damped_quotient(num: torch.Tensor, den: torch.Tensor) -> torch.Tensor:
+    """fwi_selftest_damped_quotient: num / den as the stencil kernels divide by
+    the damping factor 1 + eta (den in [1, 2^126))."""
+    if num.shape != den.shape:
+        raise ValueError("num and den must have one shape")
+    out = torch.empty_like(num)
+    check("fwi_selftest_damped_quotient", _lib.load().fwi_selftest_damped_quotient(
+        _dev(num, torch.float32, "num"), _dev(den, torch.float32, "den"), _dev(out, torch.float32, "out"),
+        num.numel(), _stream()))
+    return out

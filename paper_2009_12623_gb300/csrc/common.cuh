@@ -186,6 +186,7 @@ cudaError_t inject_multi_launch(int nfields, const RecTask* t, const int* nrec, 
 // Bounded-wait self-test: one CTA waits `polls` polls on an mbarrier that
 // never completes and flags ST_TIMEOUT in *d_status.
 cudaError_t wait_selftest_launch(int* d_status, long polls, cudaStream_t s);
+cudaError_t quotient_selftest_launch(const float* num, const float* den, float* out, long n, cudaStream_t s);
 
 // Residual r = a - b, FP64 half-sum-of-squares added to *d_acc; dot product
 // likewise.  `part` holds reduce_scratch_doubles() doubles; the summation

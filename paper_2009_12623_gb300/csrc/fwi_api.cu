@@ -905,6 +905,18 @@ int fwi_selftest_bounded_wait(long long polls, void* stream) {
   return rc ? rc : status_from_flags(flags);
 }
 
+int fwi_selftest_damped_quotient(const float* d_num, const float* d_den, float* d_out, long long n,
+                                 void* stream) {
+  if (n < 0 || (n > 0 && (!d_num || !d_den || !d_out))) return FWI_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (quotient_selftest_launch(d_num, d_den, d_out, (long)n, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FWI_ERR_CUDA;
+  }
+  return FWI_OK;
+}
+
 size_t zfp_max_compressed_bytes(int nx, int ny, int nz) {
   if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
   return zlayout(nx, ny, nz).max_bytes;

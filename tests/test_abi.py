@@ -109,3 +109,5 @@ def test_selftest_argument_validation_without_gpu(fwi_lib):
     from paper_2009_12623_gb300 import _lib
     assert fwi_lib.fwi_selftest_bounded_wait(0, None) == _lib.FWI_ERR_ARG
     assert fwi_lib.fwi_selftest_bounded_wait((1 << 20) + 1, None) == _lib.FWI_ERR_ARG
+    assert fwi_lib.fwi_selftest_damped_quotient(None, None, None, -1, None) == _lib.FWI_ERR_ARG
+    assert fwi_lib.fwi_selftest_damped_quotient(None, None, None, 4, None) == _lib.FWI_ERR_ARG
