@@ -171,6 +171,10 @@ def config_dict(args, shot, policy):
             "l2_flush": "inputs larger than L2 (0.9 GB fields)", "parallelism": "shot per GPU"}
 
 
+# kernel classes of the gradient that run alone on the sweep's stream
+IN_ORDER = ("stencil_forward", "stencil_adjoint_imaging", "zfp_decode")
+
+
 def kernel_bytes(cells, enc_bytes_per_launch):
     """Algorithmic bytes per launch (halos and scratch excluded)."""
     return {
@@ -380,7 +384,11 @@ def run_fwi(args):
     enc_bytes = stats["used_bytes"] / max(1, stats["n_checkpoints"])
     kb = kernel_bytes(cells, enc_bytes)
     timed = {k: v for k, v in prof.items() if k in kb and v[1] > 0}
-    dom = max(timed, key=lambda k: timed[k][0])
+    # The dominant kernel is the one with the most device time among those that run alone, in
+    # order, on the sweep's stream.  The encoder runs on a second stream beside the next forward
+    # step, so its event-timed duration includes the time it waits for SMs held by that step.
+    alone = [k for k in timed if k in IN_ORDER] or list(timed)
+    dom = max(alone, key=lambda k: timed[k][0])
     dom_ms, dom_n = timed[dom]
     achieved = kb[dom] / (dom_ms / dom_n / 1e3) / 1e9
     kernels = {k: {"launches": n, "total_ms": round(t, 3), "avg_us": round(1e3 * t / n, 2),
@@ -392,6 +400,8 @@ def run_fwi(args):
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)",
+            "dominant_rule": "most device time among kernels that run alone on the sweep's stream "
+                             "(the encoder overlaps the next forward step on a second stream)",
             "algorithmic_bytes_per_launch": kb[dom]}
 
     # ---- end to end through the host-memory entry point --------------------------

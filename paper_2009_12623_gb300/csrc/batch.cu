@@ -331,17 +331,19 @@ int run(fwi_batch* B, int phases, const float* d_m, const float* d_obs, const fl
     };
 
     if (B->pol.mode == FWI_CKPT_FULL) {
-      // u^k decoded into f[k & 1] on the codec stream one step ahead
+      // u^k decoded into f[k & 1] one step ahead (on the codec stream when
+      // kDecodeOverlap, else in order on s)
+      const cudaStream_t dq = kDecodeOverlap ? cs : s;
       bool used[2] = {false, false};
       auto prefetch = [&](int k) -> int {
         const int q = k & 1;
-        if (used[q]) CK(cudaStreamWaitEvent(cs, ev[4 + q], 0));
+        if (used[q]) CK(cudaStreamWaitEvent(dq, ev[4 + q], 0));
         for (int i = 0; i < S; ++i)
           if (k <= B->shots[i].sp.nt) {
-            int r = load_field(B->shots[i], slot_of(i, k, 1), B->shots[i].f[q], cs);
+            int r = load_field(B->shots[i], slot_of(i, k, 1), B->shots[i].f[q], dq);
             if (r) return r;
           }
-        CK(cudaEventRecord(ev[2 + q], cs));
+        CK(cudaEventRecord(ev[2 + q], dq));
         return FWI_OK;
       };
       if ((st = fork())) return st;

@@ -76,6 +76,25 @@ struct SWriter {
   }
 };
 
+// Coordinates of block blk (x fastest) in a grid of nbx x nby x . blocks.
+// 32-bit division whenever the block count allows it: 64-bit integer division
+// is a long software sequence on the GPU.
+__device__ __forceinline__ void block_xyz(long blk, long nbx, long nby, long nblocks, long& bx, long& by,
+                                          long& bz) {
+  if (nblocks <= 0xffffffffL) {
+    const unsigned b = (unsigned)blk, nx = (unsigned)nbx, ny = (unsigned)nby;
+    const unsigned q = b / nx;
+    bx = b - q * nx;
+    by = q % ny;
+    bz = q / ny;
+  } else {
+    const long q = blk / nbx;
+    bx = blk - q * nbx;
+    by = q % nby;
+    bz = q / nby;
+  }
+}
+
 struct EncArgs {
   const float* in;
   bool vec_ok;  // rows 16-byte aligned (pitch % 4 == 0 and aligned base)
@@ -116,7 +135,8 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, 4) k_encode_chained(EncArgs
   uint32_t u[64];
   int planes = 0, emax = 0, nbits = 0;
   if (valid) {
-    const long bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
+    long bx, by, bz;
+    block_xyz(blk, a.nbx, a.nby, a.nblocks, bx, by, bz);
     const long xb = 4 * bx;
     // 16-byte row loads when the 4 x values are in range and aligned
     const bool vec = a.vec_ok && xb + 3 < a.nx;
@@ -259,7 +279,8 @@ struct StageArgs {
 };
 
 __device__ __forceinline__ void gather_block(const EncArgs& a, long blk, uint32_t* u) {
-  const long bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
+  long bx, by, bz;
+  block_xyz(blk, a.nbx, a.nby, a.nblocks, bx, by, bz);
   const long xb = 4 * bx;
   const bool vec = a.vec_ok && xb + 3 < a.nx;  // 16-byte row loads when aligned and in range
 #pragma unroll
@@ -605,7 +626,8 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(
     }
     dequantise(u, emax, planes, v);
   }
-  const long bx = blk % a.nbx, by = (blk / a.nbx) % a.nby, bz = blk / (a.nbx * a.nby);
+  long bx, by, bz;
+  block_xyz(blk, a.nbx, a.nby, a.nblocks, bx, by, bz);
   const long xb = 4 * bx;
   const bool vec = a.vec_ok && xb + 3 < a.nx;
 #pragma unroll

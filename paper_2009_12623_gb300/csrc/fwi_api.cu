@@ -549,21 +549,23 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
   if (do_fwd) CK(cudaMemsetAsync(d_peak, 0, sizeof(unsigned long long), s));
   const int minexp = lossy ? minexp_of(pol->atol) : 0;
 
-  // Codec work runs on a second stream so that compressing u^{n+1} overlaps
-  // the next stencil step (which only reads that buffer) and decoding u^{k-1}
-  // overlaps adjoint step k.  Per-buffer events order every overwrite after
-  // the codec reads or writes that buffer.
+  // Encoding runs on a second stream so that compressing u^{n+1} overlaps
+  // the next stencil step (which only reads that buffer); decoding u^{k-1}
+  // runs in order before adjoint step k (kDecodeOverlap).  Per-buffer events
+  // order every overwrite after the codec reads or writes that buffer.
   CodecStream cs(s);
   if (!cs.ok) return FWI_ERR_CUDA;
   s = cs.main;  // the sweep's own stream from here on
+  const cudaStream_t enc_s = cs.s;
+  const cudaStream_t dec_s = kDecodeOverlap ? cs.s : s;
   auto store_field = [&](const float* f, int j) -> int {
     if (lossy) {
-      CK(slot_offset_launch(offs, sizes, j, cs.s));
+      CK(slot_offset_launch(offs, sizes, j, enc_s));
       CK(zfp_encode_launch(f, G, minexp, store->arena, offs + j, store->capacity, sizes + j,
-                           sw.d_status, scratch, cs.s));
-      CK(track_peak_launch(offs, sizes, j, d_peak, cs.s));
+                           sw.d_status, scratch, enc_s));
+      CK(track_peak_launch(offs, sizes, j, d_peak, enc_s));
     } else {
-      CK(cudaMemcpyAsync(store->arena + (size_t)j * raw_slot, f, fbytes, cudaMemcpyDeviceToDevice, cs.s));
+      CK(cudaMemcpyAsync(store->arena + (size_t)j * raw_slot, f, fbytes, cudaMemcpyDeviceToDevice, enc_s));
     }
     return FWI_OK;
   };
@@ -587,12 +589,15 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
   int d_step[2] = {-1, -1};
   const bool full = pol->mode == FWI_CKPT_FULL || pol->mode == FWI_CKPT_SUBSAMPLE;
   int next_buf = 0;
-  auto issue_decode = [&](int k) -> int {  // u^k into the next decode buffer, on the codec stream
+  auto issue_decode = [&](int k) -> int {  // u^k into the next decode buffer, on dec_s
     const int b = next_buf;
     next_buf ^= 1;
-    if (d_inuse[b]) CK(cudaStreamWaitEvent(cs.s, d_used[b], 0));
-    if ((st = load_field(slot[{k, 1}], dbuf[b], cs.s))) return st;
-    CK(cudaEventRecord(d_ready[b], cs.s));
+    // in order on the sweep's stream: first wait for every encode issued so
+    // far (the state may have been stored moments ago)
+    if (!kDecodeOverlap) CK(cs.join());
+    if (d_inuse[b]) CK(cudaStreamWaitEvent(dec_s, d_used[b], 0));
+    if ((st = load_field(slot[{k, 1}], dbuf[b], dec_s))) return st;
+    CK(cudaEventRecord(d_ready[b], dec_s));
     d_issued[b] = true;
     d_step[b] = k;
     return FWI_OK;
@@ -644,15 +649,15 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
         if (a.step > 0) {
           if (state_step != a.step) return FWI_ERR_ARG;
           CK(cudaEventRecord(ev_adv, s));
-          CK(cudaStreamWaitEvent(cs.s, ev_adv, 0));
+          CK(cudaStreamWaitEvent(enc_s, ev_adv, 0));
           const int j1 = binom ? bslot((int)bstack.size(), 1) : slot[{a.step, 1}];
           const int j0 = binom ? bslot((int)bstack.size(), 0) : (a.arg == 2 ? slot[{a.step, 0}] : -1);
           if ((st = store_field(fcur, j1))) return st;
           if (a.arg == 2 && (st = store_field(fprev, j0))) return st;
-          CK(cudaEventRecord(f_read[fidx(fcur)], cs.s));
+          CK(cudaEventRecord(f_read[fidx(fcur)], enc_s));
           f_pending[fidx(fcur)] = true;
           if (a.arg == 2) {
-            CK(cudaEventRecord(f_read[fidx(fprev)], cs.s));
+            CK(cudaEventRecord(f_read[fidx(fprev)], enc_s));
             f_pending[fidx(fprev)] = true;
           }
           if (binom) bstack.push_back(a.step);

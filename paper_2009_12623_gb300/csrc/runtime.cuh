@@ -98,6 +98,19 @@ int minexp_of(double atol) {
   return e - 1;
 }
 
+// Where the reverse sweeps decode u^{k-1}: beside adjoint step k on the
+// codec stream (1), or in order on the sweep's own stream before it (0).  In
+// order is faster on GB300 (881x881x287, full history at atol 1e-4: reverse
+// phase 3.80 s against 4.15 s overlapped, where the adjoint stencil ran
+// 1.37-1.71 ms per step instead of 1.08 ms): the memory-bound stencil and
+// the decoder, which writes a whole field per step, contend for HBM and L2
+// rather than filling each other's idle cycles.  Encoding keeps its overlap
+// with the next forward step (forward phase 3.06 s against 3.13 s in order).
+#ifndef FWI_DECODE_OVERLAP
+#define FWI_DECODE_OVERLAP 0
+#endif
+constexpr bool kDecodeOverlap = FWI_DECODE_OVERLAP != 0;
+
 #define CK(x)                          \
   do {                                 \
     if ((x) != cudaSuccess) {          \
