@@ -222,8 +222,10 @@ int run(fwi_batch* B, int phases, const float* d_m, const float* d_obs, const fl
     NR.clear();
   };
 
+  PhaseRange phase;
   // ---- forward sweep: u^{n+1} for all shots with n < nt, records, checkpoints
   if (fwd) {
+    phase.enter(kPhaseForward);
     if (B->lossy) CK(cudaMemsetAsync(B->d_offs, 0, sizeof(unsigned long long) * (2 * B->nslots + 1), s));
     for (BShot& sh : B->shots) {
       CK(cudaMemsetAsync(sh.f[0], 0, sh.G.cells() * 4, s));
@@ -282,6 +284,7 @@ int run(fwi_batch* B, int phases, const float* d_m, const float* d_obs, const fl
 
   // ---- reverse sweep -------------------------------------------------------
   if (rev) {
+    phase.enter(kPhaseReverse);
     if ((st = join())) return st;  // every checkpoint is stored
     std::vector<const float*> resid(S);
     std::vector<float*> lc(S), ln(S);

@@ -620,10 +620,12 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
     CK(cudaMemcpyAsync(fcur, (uint8_t*)store->carry + fbytes, fbytes, cudaMemcpyDeviceToDevice, s));
     state_step = N;
   }
+  PhaseRange phase;
   for (size_t ai = 0; ai < sc.a.size(); ++ai) {
     const fwi_action& a = sc.a[ai];
     if ((ai < first_rev && !do_fwd) || (ai >= first_rev && !do_rev)) continue;
     if (ai == first_rev && do_fwd && !do_rev && binom) break;
+    phase.enter(ai < first_rev ? kPhaseForward : kPhaseReverse);
     switch (a.kind) {
       case FWI_ACT_ADVANCE:
       case FWI_ACT_RECOMPUTE: {

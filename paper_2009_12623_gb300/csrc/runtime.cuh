@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -85,6 +86,25 @@ struct CodecStream {
     cudaGetLastError();
   }
 };
+
+// NVTX range of the sweep phase being enqueued ("fwi forward sweep",
+// "fwi reverse sweep", ...), for profilers: nsys shows it on the host
+// timeline, and `ncu --nvtx --nvtx-include "fwi reverse sweep/"` profiles
+// only that phase's kernels.  Costs nothing when no tool is attached.
+struct PhaseRange {
+  const char* name = nullptr;
+  void enter(const char* n) {
+    if (n == name) return;
+    if (name) nvtxRangePop();
+    nvtxRangePushA(n);
+    name = n;
+  }
+  ~PhaseRange() {
+    if (name) nvtxRangePop();
+  }
+};
+constexpr const char* kPhaseForward = "fwi forward sweep";
+constexpr const char* kPhaseReverse = "fwi reverse sweep";
 
 bool geometry_ok(const fwi_geometry* g) {
   return g && g->nx > 0 && g->ny > 0 && g->nz > 0 && g->nt >= 0 && g->h > 0 && g->dt > 0 &&
