@@ -13,6 +13,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import os
 import time
 
 import numpy as np
@@ -46,16 +47,28 @@ def misfit_and_gradient_batched(c: torch.Tensor, plan: api.Batch, wavelets, d_ob
 
 
 def descend(c0: torch.Tensor, grad_fn, iters: int, step: float, vmin: float, vmax: float,
-            mask: torch.Tensor | None):
+            mask: torch.Tensor | None, resume: dict | None = None, on_iter=None):
     """Steepest descent on velocity.  Every gradient is divided by the size of
     the first iteration's gradient (its largest magnitude), so the first
     update changes the model by at most step x mean velocity and later
-    updates shrink with the gradient; returns (c, misfit history, first gradient)."""
+    updates shrink with the gradient; returns (c, misfit history, first gradient).
+
+    `resume` (a dict from load_state) continues an earlier run where it
+    stopped: its model, misfit history, gradient scale and the starting
+    model's mean velocity, so that the continued iterations are the ones an
+    uninterrupted run would take.  `on_iter(state)` is called after every
+    iteration with that dict (save_state writes it to a file)."""
     c = c0.clone()
     hist = []
     g0 = None
+    cmean = float(c0.mean())
+    if resume is not None:
+        c = resume["c"].to(device=c0.device, dtype=c0.dtype).clone()
+        hist = list(resume["hist"])
+        g0 = resume["g0"]
+        cmean = resume["c0_mean"]
     first = None
-    for _ in range(iters):
+    for _ in range(len(hist), iters):
         phi, g = grad_fn(c)
         if mask is not None:
             g = g * mask
@@ -63,13 +76,32 @@ def descend(c0: torch.Tensor, grad_fn, iters: int, step: float, vmin: float, vma
             g0 = float(g.abs().max())
             first = g.clone()
         hist.append(phi)
-        c = (c - step * float(c0.mean()) * g / g0).clamp(vmin, vmax)
+        c = (c - step * cmean * g / g0).clamp(vmin, vmax)
+        if on_iter is not None:
+            on_iter({"c": c, "hist": hist, "g0": g0, "c0_mean": cmean})
     return c, hist, first
+
+
+def save_state(path: str, state: dict) -> None:
+    """Write a descent state (model, misfit history, gradient scale, starting
+    mean velocity) to an .npz file, atomically."""
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, c=state["c"].detach().cpu().numpy(), hist=np.asarray(state["hist"], np.float64),
+             g0=np.float64(state["g0"]), c0_mean=np.float64(state["c0_mean"]))
+    os.replace(tmp, path)
+
+
+def load_state(path: str) -> dict:
+    """Read a descent state written by save_state."""
+    with np.load(path) as z:
+        return {"c": torch.from_numpy(z["c"]), "hist": [float(x) for x in z["hist"]],
+                "g0": float(z["g0"]), "c0_mean": float(z["c0_mean"])}
 
 
 def invert(c0: torch.Tensor, shots, d_obs, iters: int = 10, mode=api.FWI_CKPT_FULL, k: int = 1,
            atol: float = 1e-4, step: float = 0.02, store_bytes: int = 16 << 30,
-           vmin: float = 1400.0, vmax: float = 6500.0, mask: torch.Tensor | None = None):
+           vmin: float = 1400.0, vmax: float = 6500.0, mask: torch.Tensor | None = None,
+           resume: dict | None = None, on_iter=None):
     """Steepest descent with one checkpointed gradient call per shot; each
     shot's backward runs right after its forward, so one store serves them
     all.  Returns (c, misfit history)."""
@@ -77,7 +109,7 @@ def invert(c0: torch.Tensor, shots, d_obs, iters: int = 10, mode=api.FWI_CKPT_FU
     stores = [store] * len(shots)
     try:
         c, hist, _ = descend(c0, lambda cc: misfit_and_gradient(cc, shots, d_obs, stores, mode, k, atol),
-                             iters, step, vmin, vmax, mask)
+                             iters, step, vmin, vmax, mask, resume, on_iter)
     finally:
         store.close()
     return c, hist
@@ -85,10 +117,10 @@ def invert(c0: torch.Tensor, shots, d_obs, iters: int = 10, mode=api.FWI_CKPT_FU
 
 def invert_batched(c0: torch.Tensor, plan: api.Batch, wavelets, d_obs_flat: torch.Tensor, iters: int = 10,
                    step: float = 0.02, vmin: float = 1400.0, vmax: float = 6500.0,
-                   mask: torch.Tensor | None = None):
+                   mask: torch.Tensor | None = None, resume: dict | None = None, on_iter=None):
     """Steepest descent through a batch plan (all shots per launch)."""
     c, hist, _ = descend(c0, lambda cc: misfit_and_gradient_batched(cc, plan, wavelets, d_obs_flat),
-                         iters, step, vmin, vmax, mask)
+                         iters, step, vmin, vmax, mask, resume, on_iter)
     return c, hist
 
 
@@ -102,7 +134,11 @@ def _main():
     p.add_argument("--iters", type=int, default=10)
     p.add_argument("--atol", type=float, default=1e-4)
     p.add_argument("--per-shot", action="store_true", help="one gradient call per shot instead of a batch plan")
+    p.add_argument("--save", default=None, help="write the descent state (.npz) after every iteration")
+    p.add_argument("--resume", default=None, help="continue from a state written by --save")
     a = p.parse_args()
+    resume = load_state(a.resume) if a.resume else None
+    on_iter = (lambda st: save_state(a.save, st)) if a.save else None
     nx, ny, nz = (int(v) for v in a.grid.split(","))
     dev = torch.device("cuda")
     nbl = min(20, nz // 6)
@@ -129,13 +165,14 @@ def _main():
     interior[nbl:nz - nbl, nbl:ny - nbl, nbl:nx - nbl] = 1.0
     t0 = time.time()
     if a.per_shot:
-        c, hist = invert(c0, shots, d_obs, iters=a.iters, atol=a.atol, mask=interior)
+        c, hist = invert(c0, shots, d_obs, iters=a.iters, atol=a.atol, mask=interior, resume=resume,
+                         on_iter=on_iter)
     else:
         specs = [api.ShotSpec(0, 0, 0, nx, ny, nz, nt, s, rec.cpu().numpy()) for s in srcs]
         with api.Batch(geom, specs, mode=api.FWI_CKPT_FULL, atol=a.atol, arena_bytes=64 << 30,
                        graph=True, tune=True) as plan:
             c, hist = invert_batched(c0, plan, [w] * len(srcs), plan.concat(d_obs), iters=a.iters,
-                                     mask=interior)
+                                     mask=interior, resume=resume, on_iter=on_iter)
     torch.cuda.synchronize()
     err0 = float(torch.linalg.vector_norm(c0 - torch.from_numpy(v_true).to(dev)))
     err = float(torch.linalg.vector_norm(c - torch.from_numpy(v_true).to(dev)))
