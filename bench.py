@@ -46,11 +46,13 @@ def parse():
     p.add_argument("--no-verify", action="store_true")
     p.add_argument("--arena-gb", type=float, default=0.0,
                    help="checkpoint arena size (0 = all free memory minus the working set)")
-    p.add_argument("--workload", default="overthrust", choices=["overthrust", "batch", "fwi", "codec", "tradeoff"],
+    p.add_argument("--workload", default="overthrust",
+                   choices=["overthrust", "batch", "fwi", "codec", "tradeoff", "restart"],
                    help="batch: 32-shot survey, batched plan against one call per shot; "
                         "fwi: 16-shot inversion through autograd, batched against per shot; "
                         "codec: 512^3 shell snapshots, atol sweep; "
-                        "tradeoff: gradient error vs memory for compression, subsampling, binomial")
+                        "tradeoff: gradient error vs memory for compression, subsampling, binomial; "
+                        "restart: error of a forward run continued from a lossy checkpoint")
     p.add_argument("--iters", type=int, default=10, help="fwi workload: descent iterations per path")
     p.add_argument("--shots", type=int, default=32)
     p.add_argument("--ckpt-k", type=int, default=10, help="batch workload: checkpoint pair every K steps")
@@ -844,6 +846,66 @@ def run_tradeoff(args):
         print(json.dumps(line), flush=True)
 
 
+def run_restart(args):
+    """The forward-propagation experiment of Sec. 4 on the Overthrust-shaped
+    grid (881 x 881 x 287, dt = 1.75 ms, 8 Hz): run 550 steps, compress the
+    state pair (u^549, u^550) at atol, continue 550 more steps from the lossy
+    and from the exact pair, and record the L_inf and L2 norms of the
+    difference of the two runs (FP64 reductions on the GPU) after every step
+    for the first 10 steps, then every 10 steps."""
+    import numpy as np
+    import torch
+    ws, rank, local, pg = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_12623_gb300 import api, synth
+    t1, t2 = 550, 550
+    shot = synth.overthrust_like_shot(nt=t1 + t2)
+    g = shot.geom
+    m = torch.from_numpy(synth.slowness2(shot.v0)).to(dev)
+    rec = torch.from_numpy(shot.rec[:1]).to(dev)
+    w = shot.wavelet
+    geo = lambda nt: api.Geometry(**{**g.__dict__, "nt": nt})  # noqa: E731
+    _, up, uc = api.forward(geo(t1), m, w[:t1], shot.src, rec, return_state=True)
+    marks = list(range(1, 11)) + list(range(20, t2 + 1, 10))
+    runs = []
+    for atol in (1e-6, 1e-4):
+        exact = [up.clone(), uc.clone()]
+        streams = [api.zfp_compress(f, atol) for f in exact]
+        lossy = [api.zfp_decompress(s_, f.shape) for s_, f in zip(streams, exact)]
+        cf = 2 * exact[0].numel() * 4 / sum(int(s_.numel()) for s_ in streams)
+        e0 = float((lossy[1] - exact[1]).abs().max())
+        done, curve = 0, []
+        for n in marks:
+            k = n - done
+            wk = w[t1 + done:t1 + n]
+            _, a0, a1 = api.forward(geo(k), m, wk, shot.src, rec, u_prev_init=exact[0], u_cur_init=exact[1],
+                                    return_state=True)
+            _, b0, b1 = api.forward(geo(k), m, wk, shot.src, rec, u_prev_init=lossy[0], u_cur_init=lossy[1],
+                                    return_state=True)
+            exact, lossy, done = [a0, a1], [b0, b1], n
+            d = a1 - b1
+            curve.append({"steps": n, "linf": float(d.abs().max()), "l2": float(np.sqrt(api.dot_f64(d, d))),
+                          "field_linf": float(a1.abs().max())})
+        l2 = [c["l2"] for c in curve]
+        runs.append({"atol": atol, "checkpoint_cf": cf, "restart_linf": e0, "peak_l2_at_step": marks[int(np.argmax(l2))],
+                     "final_over_peak_l2": l2[-1] / max(l2), "max_linf_over_atol": max(c["linf"] for c in curve) / atol,
+                     "curve": curve})
+        del exact, lossy, streams
+    line = {"metric": "error of a forward run restarted from a lossy checkpoint", "value": None, "unit": None,
+            "n_gpus": ws, "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": None, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"overthrust-like {g.nx}x{g.ny}x{g.nz} at {g.h:.0f} m, dt={g.dt * 1e3:.2f} ms, "
+                                   f"8 Hz; {t1} steps, state pair compressed, {t2} steps continued"},
+            "restart": runs}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -856,6 +918,8 @@ def main():
         run_codec(args)
     elif args.workload == "tradeoff":
         run_tradeoff(args)
+    elif args.workload == "restart":
+        run_restart(args)
     else:
         run_fwi(args)
 
