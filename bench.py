@@ -406,6 +406,10 @@ def run_fwi(args):
                              "(the encoder overlaps the next forward step on a second stream)",
             "algorithmic_bytes_per_launch": kb[dom]}
 
+    # compressibility over the simulation (Sec. 4.1): CF of each tenth of the stored states
+    sb = store.slot_bytes().astype(np.float64)
+    cf_tenths = [round(float(cells * 4 * len(c) / c.sum()), 1) for c in np.array_split(sb, 10) if c.size]
+
     # ---- end to end through the host-memory entry point --------------------------
     d_obs_v = d_obs
     e2e = None
@@ -480,7 +484,8 @@ def run_fwi(args):
                 "kernels": kernels,
                 "checkpoint_store": {"used_GiB": round(stats["used_bytes"] / 2**30, 2),
                                      "compression_factor": round(stats["raw_bytes"] / max(1, stats["used_bytes"]), 2),
-                                     "checkpoints": stats["n_checkpoints"]},
+                                     "checkpoints": stats["n_checkpoints"],
+                                     "cf_by_tenth_of_run": cf_tenths},
                 "misfit": phi, "gradient_error": verify}
         print(json.dumps(line), flush=True)
     store.close()

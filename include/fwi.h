@@ -121,6 +121,17 @@ typedef struct {
 } fwi_store_stats;
 int fwi_ckpt_store_stats(const fwi_ckpt_store* st, fwi_store_stats* out);
 
+/* Bytes of each checkpoint slot the last forward sweep filled, in slot order
+ * (full history: slot j holds u^{j+1}; every-K: the pairs in schedule order,
+ * u^k before u^{k-1}; binomial: the last state held by each slot), written to
+ * h_bytes[0 .. min(cap, n) - 1] with n, the slot count, in *n_out (0 while
+ * the store holds no forward sweep).  Compressed stores report each stream's size, raw
+ * stores the field size.  This is how the compressibility of the wavefield
+ * over the simulation (Sec. 4.1) is read.  Synchronous (device-to-host copy).
+ * FWI_ERR_ARG for a null store or n_out, a negative cap, or a null h_bytes
+ * with cap > 0. */
+int fwi_ckpt_store_slot_bytes(const fwi_ckpt_store* st, unsigned long long* h_bytes, int cap, int* n_out);
+
 /* ---- forward modelling (Sec. 2, Eq. (1)-(2)) ------------------------------ */
 /* Runs u^{n+1} for n = 0..nt-1 from the zero state (or from the given pair
  * d_u_prev_init = u^{-1}, d_u_cur_init = u^0) and records

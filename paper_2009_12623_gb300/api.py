@@ -115,6 +115,17 @@ class CheckpointStore:
                 "raw_bytes": s.raw_bytes, "n_checkpoints": s.n_checkpoints,
                 "overflowed": bool(s.overflowed)}
 
+    def slot_bytes(self) -> np.ndarray:
+        """fwi_ckpt_store_slot_bytes: bytes of each checkpoint slot of the last
+        forward sweep, in slot order (full history: u^1, u^2, ...)."""
+        L = _lib.load()
+        n = C.c_int(0)
+        check("fwi_ckpt_store_slot_bytes", L.fwi_ckpt_store_slot_bytes(self.handle, None, 0, C.byref(n)))
+        out = np.zeros(max(1, n.value), dtype=np.uint64)
+        check("fwi_ckpt_store_slot_bytes", L.fwi_ckpt_store_slot_bytes(
+            self.handle, out.ctypes.data_as(C.POINTER(C.c_ulonglong)), n.value, C.byref(n)))
+        return out[:n.value]
+
     def close(self):
         if self._h:
             _lib.load().fwi_ckpt_store_destroy(self._h)

@@ -407,6 +407,26 @@ int fwi_ckpt_store_stats(const fwi_ckpt_store* st, fwi_store_stats* out) {
   return FWI_OK;
 }
 
+int fwi_ckpt_store_slot_bytes(const fwi_ckpt_store* st, unsigned long long* h_bytes, int cap, int* n_out) {
+  if (!st || !n_out || cap < 0 || (cap > 0 && !h_bytes)) return FWI_ERR_ARG;
+  const int n = st->filled ? st->nslots : 0;
+  *n_out = n;
+  const int k = std::min(n, cap);
+  if (k == 0) return FWI_OK;
+  if (!st->lossy) {
+    const unsigned long long field = (unsigned long long)st->geom.nx * st->geom.ny * st->geom.nz * 4ull;
+    for (int i = 0; i < k; ++i) h_bytes[i] = field;
+    return FWI_OK;
+  }
+  if (!st->d_offs || st->slot_cap < n ||
+      cudaMemcpy(h_bytes, st->d_offs + st->slot_cap, sizeof(unsigned long long) * (size_t)k,
+                 cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return FWI_ERR_CUDA;
+  }
+  return FWI_OK;
+}
+
 int fwi_forward(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
                 int src_j, int src_k, const int* d_rec_ijk, int nrec, float* d_rec_out,
                 const float* d_u_prev_init, const float* d_u_cur_init, float* d_u_prev_out,
@@ -789,6 +809,8 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
     store->filled = true;
     store->geom = *g;
     store->pol = *pol;
+    store->nslots = nslots;
+    store->lossy = lossy;
   }
   // a binomial reverse half reuses the snapshot slots of the forward half,
   // so the store no longer holds that forward sweep

@@ -161,6 +161,8 @@ struct fwi_ckpt_store {
   unsigned long long* d_sizes = nullptr;
   int slot_cap = 0;
   bool filled = false;  // a forward sweep completed and its checkpoints are in the arena
+  int nslots = 0;       // slots the last forward sweep used
+  bool lossy = false;   // whether they hold compressed streams
   float* carry = nullptr;  // binomial: final forward state pair kept between the two halves
   size_t carry_bytes = 0;
   fwi_geometry geom{};

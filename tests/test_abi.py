@@ -111,3 +111,5 @@ def test_selftest_argument_validation_without_gpu(fwi_lib):
     assert fwi_lib.fwi_selftest_bounded_wait((1 << 20) + 1, None) == _lib.FWI_ERR_ARG
     assert fwi_lib.fwi_selftest_damped_quotient(None, None, None, -1, None) == _lib.FWI_ERR_ARG
     assert fwi_lib.fwi_selftest_damped_quotient(None, None, None, 4, None) == _lib.FWI_ERR_ARG
+    n = C.c_int(-1)
+    assert fwi_lib.fwi_ckpt_store_slot_bytes(None, None, 0, C.byref(n)) == _lib.FWI_ERR_ARG

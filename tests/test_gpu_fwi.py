@@ -346,3 +346,32 @@ def test_lossy_restart_propagation_matches_oracle(cuda, oracle):
     assert 1 <= k <= 30 and l2[k] > 1.5 * l2[0]
     assert l2[-1] < 0.8 * l2[k]
     assert linf.max() <= 2 * atol
+
+
+def test_slot_bytes_report_each_checkpoint(cuda, two_layer):
+    """fwi_ckpt_store_slot_bytes: one entry per stored state, consistent with
+    the store's totals; compressed states grow as the wave spreads through
+    the grid (the compressibility trend of Sec. 4.1); raw and every-K stores
+    report field sizes and pair slots."""
+    from paper_2009_12623_gb300 import api, synth
+    shot, d_obs = two_layer
+    g = shot.geom
+    m = _dev(cuda, synth.slowness2(shot.v0))
+    rec = _dev(cuda, shot.rec)
+    obs = _dev(cuda, np.asarray(d_obs, np.float32))
+    field = g.nx * g.ny * g.nz * 4
+    with api.CheckpointStore(1 << 30) as st:
+        assert st.slot_bytes().size == 0
+        api.gradient(g, m, shot.wavelet, shot.src, rec, obs, st, mode=api.FWI_CKPT_FULL, atol=1e-4)
+        b = st.slot_bytes().astype(np.int64)
+        s = st.stats()
+        assert b.size == g.nt == s["n_checkpoints"]
+        assert np.all(b > 0) and np.all(b <= field + 4096)
+        assert b.sum() <= s["used_bytes"] <= b.sum() + 256 * b.size
+        q = g.nt // 5
+        assert b[:q].mean() < b[-q:].mean()
+        api.gradient(g, m, shot.wavelet, shot.src, rec, obs, st, mode=api.FWI_CKPT_FULL, atol=0.0)
+        assert np.all(st.slot_bytes() == field)
+        api.gradient(g, m, shot.wavelet, shot.src, rec, obs, st, mode=api.FWI_CKPT_EVERY_K, k=10, atol=1e-4)
+        b10 = st.slot_bytes()
+        assert b10.size == st.stats()["n_checkpoints"] and b10.size % 2 == 0 and b10.size <= 2 * (g.nt // 10 + 1)
