@@ -11,12 +11,16 @@
 // consecutive blocks (4 independent warps per CTA, never synchronised with
 // each other).  The 64 coefficients of a block live in registers; two 32x32
 // bit-matrix transposes turn them into 64-bit plane masks, from which the
-// exact bit count of every plane is computed with popc/clz.  A warp scan of
-// the counts and a warp-parallel decoupled look-back across chunks (chunk
-// order is the warp's ticket order, so every predecessor is already resident)
-// give each chunk its word offset in one pass; the chunk's bits are assembled
-// in the warp's shared-memory buffer while the predecessors finish, then
-// written with coalesced 64-bit stores.  Decoding reverses this with one warp
+// exact bit count of every plane is computed with popc/clz, and a warp scan
+// of the counts places each block's bits in its chunk.  Chunk offsets: the
+// staged encoder (k_encode_stage / _compact / _place, used by the sweeps and
+// zfp_compress_fixed_accuracy) codes every chunk into a fixed staging slot,
+// scans the word counts and copies the words into place; the single-pass
+// encoder of the allocation-free entry point (k_encode_chained) finds them by
+// a warp-parallel decoupled look-back across chunks (chunk order is the
+// warp's ticket order, so every predecessor is already resident).  Either way
+// a chunk's bits are assembled in the warp's shared-memory buffer and written
+// with coalesced 64-bit stores.  Decoding reverses this with one warp
 // per chunk: the chunk's words are staged in shared memory, block offsets come
 // from a warp scan of the u16 length table, and each thread rebuilds its plane
 // masks (ctz finds every newly significant coefficient).
