@@ -19,7 +19,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# ORACLE_LIBRARY names a separately built copy of the oracle (the planted-
+# mistake tests build mutated copies and run the pins against them).
+_LIB_PATH = os.environ.get("ORACLE_LIBRARY") or os.path.join(_HERE, "liboracle.so")
 _SOURCES = ["fwi_oracle.c", "zfp_oracle.c"]
 _lock = threading.Lock()
 _lib = None
@@ -31,6 +33,8 @@ ACT_ADVANCE, ACT_STORE, ACT_RESTORE, ACT_RECOMPUTE, ACT_ADJOINT, ACT_FREE = 1, 2
 
 def build(force: bool = False) -> str:
     """Compile the oracle's C sources into ``oracle/liboracle.so`` (gcc, OpenMP)."""
+    if os.environ.get("ORACLE_LIBRARY"):
+        return _LIB_PATH  # built elsewhere, used as it is
     srcs = [os.path.join(_HERE, s) for s in _SOURCES]
     hdr = os.path.join(_HERE, "oracle.h")
     if not force and os.path.exists(_LIB_PATH):

@@ -1,0 +1,87 @@
+"""Planted mistakes: each test copies the oracle's C sources, plants one
+plausible mistake (a wrong coefficient or sign, a dropped term, an index off
+by one, a swapped operand, a wrong constant), builds that copy and runs the
+oracle's pin tests against it (ORACLE_LIBRARY).  The pins must fail for every
+mistake, so they pin the oracle to the paper and the mathematics rather than
+to itself.  The unmutated copy passes the same pins.  All on the CPU."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+STENCIL, GRADIENT, CODEC = "tests/test_oracle_stencil.py", "tests/test_oracle_gradient.py", "tests/test_oracle_codec.py"
+
+# (id, source file, text, replacement, pin file expected to catch it)
+MUTANTS = [
+    ("laplacian-coefficient-sign", "fwi_oracle.c", "-1.0 / 5.0, 8.0 / 315.0", "1.0 / 5.0, 8.0 / 315.0", STENCIL),
+    ("laplacian-dropped-z-term", "fwi_oracle.c",
+     "          acc += OC[r] * (oc_at(u, g, x, y, z + r) + oc_at(u, g, x, y, z - r));\n", "", STENCIL),
+    ("laplacian-neighbour-index", "fwi_oracle.c", "(oc_at(u, g, x + r, y, z) + oc_at(u, g, x - r, y, z))",
+     "(oc_at(u, g, x + r, y, z) + oc_at(u, g, x + r, y, z))", STENCIL),
+    ("damping-sign", "fwi_oracle.c", "double am = m[i] * idt2 - sig[i] / (2.0 * g->dt);",
+     "double am = m[i] * idt2 + sig[i] / (2.0 * g->dt);", STENCIL),
+    ("sponge-profile-power", "fwi_oracle.c", "* (d / W) * (d / W)", "* (d / W)", STENCIL),
+    ("source-one-step-late", "fwi_oracle.c", "double q = wavelet[n];", "double q = wavelet[n > 0 ? n - 1 : 0];",
+     STENCIL),
+    ("adjoint-residual-index", "fwi_oracle.c",
+     "oc_step(g, m, sig, lcur, lnext, lnext, Lb, rc, resid + (long)(k - 1) * nrec, nrec);",
+     "oc_step(g, m, sig, lcur, lnext, lnext, Lb, rc, resid + (long)(k > 1 ? k - 2 : 0) * nrec, nrec);", GRADIENT),
+    ("gradient-residual-index", "fwi_oracle.c",
+     "oc_step(g, m, sig, lcur, lnext, lnew, Lb, rc, resid + (long)(k - 1) * nrec, nrec);",
+     "oc_step(g, m, sig, lcur, lnext, lnew, Lb, rc, resid + (long)(k > 1 ? k - 2 : 0) * nrec, nrec);", GRADIENT),
+    ("imaging-sign", "fwi_oracle.c", "grad[i] -= weight * uk[i]", "grad[i] += weight * uk[i]", GRADIENT),
+    ("imaging-second-difference", "fwi_oracle.c", "(lnew[i] - 2.0 * lcur[i] + lnext[i])", "(lnew[i] - lnext[i])",
+     GRADIENT),
+    ("records-wrong-time-level", "fwi_oracle.c", "dsim[(long)s * nrec + r] = cur[rc[r]];",
+     "dsim[(long)s * nrec + r] = prev[rc[r]];", GRADIENT),
+    ("codec-guard-planes", "zfp_oracle.c", "#define ZO_G 11", "#define ZO_G 8", CODEC),
+    ("codec-fraction-bits", "zfp_oracle.c", "#define ZO_S 25", "#define ZO_S 24", CODEC),
+    ("codec-lifting-trend", "zfp_oracle.c", "  d0 = d0 - zo_half(D);\n  d1 = d1 - zo_half(D);\n  p[0] = S;",
+     "  d1 = d1 - zo_half(D);\n  p[0] = S;", CODEC),
+    ("codec-negabinary-mask", "zfp_oracle.c", "#define ZO_NBMASK 0xAAAAAAAAu", "#define ZO_NBMASK 0x55555555u", CODEC),
+    ("codec-dropped-verbatim-bit", "zfp_oracle.c",
+     "    for (int i = 0; i < n; i++)\n      if ((s = zo_put_bit(bw, (u[i] >> b) & 1u))) return s;",
+     "    for (int i = 1; i < n; i++)\n      if ((s = zo_put_bit(bw, (u[i] >> b) & 1u))) return s;", CODEC),
+]
+
+
+def _build(tmp, mutation=None):
+    """Copy the oracle sources into tmp, plant `mutation`, build liboracle.so there."""
+    for f in ("fwi_oracle.c", "zfp_oracle.c", "oracle.h"):
+        shutil.copy(os.path.join(ORACLE, f), tmp)
+    if mutation:
+        fname, old, new = mutation
+        path = os.path.join(tmp, fname)
+        src = open(path).read()
+        assert src.count(old) == 1, f"mutation text not found exactly once in {fname}: {old!r}"
+        open(path, "w").write(src.replace(old, new))
+    lib = os.path.join(tmp, "liboracle.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wno-unknown-pragmas", "-o", lib,
+                    os.path.join(tmp, "fwi_oracle.c"), os.path.join(tmp, "zfp_oracle.c"), "-lm"], check=True)
+    return lib
+
+
+def _pins(lib, test_file, stop_first=True):
+    env = dict(os.environ, ORACLE_LIBRARY=lib, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"))
+    cmd = [sys.executable, "-m", "pytest", test_file, "-q", "-m", "not gpu", "-p", "no:cacheprovider"]
+    if stop_first:
+        cmd.append("-x")
+    return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_unmutated_copy_passes_the_pins(tmp_path):
+    lib = _build(str(tmp_path))
+    for f in (STENCIL, GRADIENT, CODEC):
+        r = _pins(lib, f, stop_first=False)
+        assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("mid,fname,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(tmp_path, mid, fname, old, new, pins):
+    lib = _build(str(tmp_path), (fname, old, new))
+    r = _pins(lib, pins)
+    assert r.returncode == 1, f"{mid}: no pin in {pins} failed\n{r.stdout[-1500:]}"
