@@ -38,6 +38,11 @@ MUTANTS = [
      GRADIENT),
     ("records-wrong-time-level", "fwi_oracle.c", "dsim[(long)s * nrec + r] = cur[rc[r]];",
      "dsim[(long)s * nrec + r] = prev[rc[r]];", GRADIENT),
+    ("binomial-cost-slots-swapped", "fwi_oracle.c",
+     "c[(size_t)(n - m) * (S + 1) + (s - 1)] + c[(size_t)m * (S + 1) + s]",
+     "c[(size_t)(n - m) * (S + 1) + s] + c[(size_t)m * (S + 1) + (s - 1)]", GRADIENT),
+    ("binomial-slot-not-consumed", "fwi_oracle.c", "oc_binom_gen(b, a + m_best, n - m_best, s - 1);",
+     "oc_binom_gen(b, a + m_best, n - m_best, s);", GRADIENT),
     ("codec-guard-planes", "zfp_oracle.c", "#define ZO_G 11", "#define ZO_G 8", CODEC),
     ("codec-fraction-bits", "zfp_oracle.c", "#define ZO_S 25", "#define ZO_S 24", CODEC),
     ("codec-lifting-trend", "zfp_oracle.c", "  d0 = d0 - zo_half(D);\n  d1 = d1 - zo_half(D);\n  p[0] = S;",
