@@ -197,3 +197,29 @@ def test_batched_inversion_tracks_per_shot_inversion(cuda):
         c2, h2 = invert.invert_batched(c0, plan, [w] * 3, plan.concat(d_obs), iters=3, step=0.01)
     assert np.allclose(h1, h2, rtol=1e-5), (h1, h2)
     assert float(torch.linalg.vector_norm(c1 - c2)) <= 1e-4 * float(torch.linalg.vector_norm(c1 - c0))
+
+
+def test_stacking_does_not_accumulate_compression_errors(cuda):
+    """Sec. 4's stacking observation on the GPU path: the stacked gradient's
+    relative error from compressed checkpoints (atol 1e-2) is at most the
+    worst single shot's, and the batch plan's stacked gradient has that same
+    error (it is bitwise the sum of the per-shot calls)."""
+    from paper_2009_12623_gb300 import api
+    sv = _survey(seed=11)
+    m, w, d_obs = _setup(cuda, sv)
+
+    def per_shot(atol):
+        with api.CheckpointStore(1 << 28) as st:
+            return [api.gradient_per_shot(sv.geom, m, [s], [wi], [d], st, mode=1, atol=atol)[0]
+                    for s, wi, d in zip(sv.shots, w, d_obs)]
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm((a - b).double()) / torch.linalg.vector_norm(b.double()))
+
+    raw, lossy = per_shot(0.0), per_shot(1e-2)
+    per = [rel(a, b) for a, b in zip(lossy, raw)]
+    stacked = rel(sum(lossy), sum(raw))
+    assert 0 < stacked <= max(per), (stacked, per)
+    with api.Batch(sv.geom, sv.shots, mode=1, atol=1e-2, arena_bytes=1 << 29) as b:
+        g, _ = b.gradient(m, w, b.concat(d_obs))
+    assert rel(g, sum(raw)) == pytest.approx(stacked, rel=1e-3)
