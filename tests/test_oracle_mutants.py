@@ -14,6 +14,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
 STENCIL, GRADIENT, CODEC = "tests/test_oracle_stencil.py", "tests/test_oracle_gradient.py", "tests/test_oracle_codec.py"
+BATCH = "tests/test_oracle_batch.py"
 
 # (id, source file, text, replacement, pin file expected to catch it)
 MUTANTS = [
@@ -43,6 +44,12 @@ MUTANTS = [
      "c[(size_t)(n - m) * (S + 1) + s] + c[(size_t)m * (S + 1) + (s - 1)]", GRADIENT),
     ("binomial-slot-not-consumed", "fwi_oracle.c", "oc_binom_gen(b, a + m_best, n - m_best, s - 1);",
      "oc_binom_gen(b, a + m_best, n - m_best, s);", GRADIENT),
+    ("batch-stacked-at-grid-origin", "fwi_oracle.c",
+     "            grad[(sh->x0 + i) + (long)g->nx * ((sh->y0 + j) + (long)g->ny * (sh->z0 + k))] +=",
+     "            grad[i + (long)g->nx * ((sh->y0 + j) + (long)g->ny * (sh->z0 + k))] +=", BATCH),
+    ("batch-model-window-at-grid-origin", "fwi_oracle.c",
+     "              m[(sh->x0 + i) + (long)g->nx * ((sh->y0 + j) + (long)g->ny * (sh->z0 + k))];",
+     "              m[i + (long)g->nx * ((sh->y0 + j) + (long)g->ny * (sh->z0 + k))];", BATCH),
     ("codec-guard-planes", "zfp_oracle.c", "#define ZO_G 11", "#define ZO_G 8", CODEC),
     ("codec-fraction-bits", "zfp_oracle.c", "#define ZO_S 25", "#define ZO_S 24", CODEC),
     ("codec-lifting-trend", "zfp_oracle.c", "  d0 = d0 - zo_half(D);\n  d1 = d1 - zo_half(D);\n  p[0] = S;",
