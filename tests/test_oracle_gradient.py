@@ -211,6 +211,20 @@ def test_subsampling_f1_is_full_history(oracle):
     assert np.array_equal(g_full, g_s) and phi == phi_s
 
 
+def test_subsampling_weighted_sum_estimates_full_sum(oracle):
+    """Imaging every f-th step with weight f is a rectangle-rule estimate of
+    the full sum over steps (Sec. 4.7): for small f the subsampled gradient's
+    component along the full gradient is the full gradient's size (within
+    10%), where an unweighted subsample would give about 1/f of it."""
+    g, m, q, src, rec = _case(oracle)
+    dobs = _obs(oracle, g, m, q, src, rec)
+    g_full, *_ = oracle.gradient(g, m, q, src, rec, dobs)
+    for f in (2, 3, 4):
+        gs, *_ = oracle.gradient(g, m, q, src, rec, dobs, mode=oracle.CKPT_SUBSAMPLE, k=f)
+        proj = np.vdot(gs, g_full) / np.vdot(g_full, g_full)
+        assert abs(proj - 1.0) < 0.1, (f, proj)
+
+
 def test_subsampling_error_grows_with_factor(oracle):
     """Subsampled imaging (Sec. 4.7): the gradient's angle to the full one
     grows with the subsampling factor while the stored states shrink as 1/f."""

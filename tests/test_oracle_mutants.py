@@ -35,6 +35,7 @@ MUTANTS = [
      "oc_step(g, m, sig, lcur, lnext, lnew, Lb, rc, resid + (long)(k - 1) * nrec, nrec);",
      "oc_step(g, m, sig, lcur, lnext, lnew, Lb, rc, resid + (long)(k > 1 ? k - 2 : 0) * nrec, nrec);", GRADIENT),
     ("imaging-sign", "fwi_oracle.c", "grad[i] -= weight * uk[i]", "grad[i] += weight * uk[i]", GRADIENT),
+    ("subsampling-weight-dropped", "fwi_oracle.c", "grad[i] -= weight * uk[i]", "grad[i] -= uk[i]", GRADIENT),
     ("imaging-second-difference", "fwi_oracle.c", "(lnew[i] - 2.0 * lcur[i] + lnext[i])", "(lnew[i] - lnext[i])",
      GRADIENT),
     ("records-wrong-time-level", "fwi_oracle.c", "dsim[(long)s * nrec + r] = cur[rc[r]];",
