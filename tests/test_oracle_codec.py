@@ -57,6 +57,20 @@ def test_lift4_exhaustive_invertible(oracle):
         assert np.array_equal(oracle.zfp_lift4(oracle.zfp_lift4(x), inverse=True), x)
 
 
+def test_lift4_means_are_floor_means(oracle):
+    """The forward lifting's averages are floor means (rounding toward minus
+    infinity, an arithmetic shift), as the format states: S is the floor mean
+    of the two pairs' floor means and D their difference, on every input in
+    [-8, 7]^4 (truncation toward zero differs on negative odd sums)."""
+    r = np.arange(-8, 8)
+    grid = np.stack(np.meshgrid(r, r, r, r, indexing="ij"), -1).reshape(-1, 4)
+    for x in grid:
+        a = (int(x[0]) + int(x[1])) // 2
+        b = (int(x[2]) + int(x[3])) // 2
+        out = oracle.zfp_lift4(x)
+        assert out[0] == (a + b) // 2 and out[1] == b - a, (x, out)
+
+
 def test_lift4_random_large_invertible(oracle):
     rng = np.random.default_rng(1)
     for x in rng.integers(-2 ** 28, 2 ** 28, size=(3000, 4)):
@@ -209,6 +223,22 @@ def test_lossless_planes_reproduce_truncated_integers(oracle):
         out, _ = oracle.zfp_decode_block(words, n, minexp)
         expect = np.ldexp(q.astype(np.float64), emax - 25).astype(np.float32)
         assert np.array_equal(out, expect)
+
+
+def test_thirty_and_thirty_one_planes_are_coded_losslessly(oracle):
+    """A block whose plane count comes out as 30 or 31 (emax - minexp = 19 or
+    20) must be coded with all 32 planes -- dropping one or two planes would
+    break the error bound (test_guard_planes_are_needed_for_small_k) -- so it
+    decodes to its truncated block-floating-point integers exactly."""
+    rng = np.random.default_rng(13)
+    for v in _blocks(rng, 120):
+        emax = int(np.frexp(np.float64(np.abs(v).max()))[1])
+        for d in (19, 20):
+            q, e2, planes = oracle.zfp_block_quantise(v, emax - d)
+            assert e2 == emax and planes == 32, (d, planes)
+            words, n = oracle.zfp_encode_block(v, emax - d)
+            out, _ = oracle.zfp_decode_block(words, n, emax - d)
+            assert np.array_equal(out, np.ldexp(q.astype(np.float64), emax - 25).astype(np.float32))
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (3, 5, 7), (9, 10, 11), (8, 8, 8), (13, 4, 17)])

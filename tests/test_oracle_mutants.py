@@ -51,6 +51,22 @@ MUTANTS = [
     ("batch-model-window-at-grid-origin", "fwi_oracle.c",
      "              m[(sh->x0 + i) + (long)g->nx * ((sh->y0 + j) + (long)g->ny * (sh->z0 + k))];",
      "              m[i + (long)g->nx * ((sh->y0 + j) + (long)g->ny * (sh->z0 + k))];", BATCH),
+    ("laplacian-missing-h2", "fwi_oracle.c", "double ih2 = 1.0 / (g->h * g->h);", "double ih2 = 1.0 / g->h;", STENCIL),
+    ("laplacian-centre-weight", "fwi_oracle.c", "double acc = 3.0 * OC[0] * c;", "double acc = OC[0] * c;", STENCIL),
+    ("source-doubled", "fwi_oracle.c", "Lbuf[cell[i]] += val[i];", "Lbuf[cell[i]] += 2.0 * val[i];", STENCIL),
+    ("leapfrog-factor-two", "fwi_oracle.c", "out[i] = (2.0 * m[i] * idt2 * cur[i]", "out[i] = (m[i] * idt2 * cur[i]",
+     STENCIL),
+    ("damping-missing-in-a-plus", "fwi_oracle.c", "double ap = m[i] * idt2 + sig[i] / (2.0 * g->dt);",
+     "double ap = m[i] * idt2;", STENCIL),
+    ("sponge-depth-off-by-one", "fwi_oracle.c", "if (i < nbl) d = (nbl - i) * h;", "if (i < nbl) d = (nbl - i - 1) * h;",
+     STENCIL),
+    ("misfit-missing-half", "fwi_oracle.c", "phi += 0.5 * resid[i] * resid[i];", "phi += resid[i] * resid[i];",
+     GRADIENT),
+    ("residual-sign", "fwi_oracle.c", "resid[i] = dsim[i] - d_obs[i];", "resid[i] = d_obs[i] - dsim[i];", GRADIENT),
+    ("codec-dequantise-exponent", "zfp_oracle.c", "ldexp((double)q[i], emax - ZO_S)", "ldexp((double)q[i], emax - ZO_S + 1)",
+     CODEC),
+    ("codec-half-truncates", "zfp_oracle.c", "return (int32_t)floor((double)a / 2.0);", "return a / 2;", CODEC),
+    ("codec-no-plane-raise", "zfp_oracle.c", "if (p == 30 || p == 31) p = 32;", "if (p == 31) p = 32;", CODEC),
     ("codec-guard-planes", "zfp_oracle.c", "#define ZO_G 11", "#define ZO_G 8", CODEC),
     ("codec-fraction-bits", "zfp_oracle.c", "#define ZO_S 25", "#define ZO_S 24", CODEC),
     ("codec-lifting-trend", "zfp_oracle.c", "  d0 = d0 - zo_half(D);\n  d1 = d1 - zo_half(D);\n  p[0] = S;",
