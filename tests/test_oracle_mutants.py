@@ -8,8 +8,7 @@ import os
 import shutil
 import subprocess
 import sys
-
-import pytest
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
@@ -94,8 +93,9 @@ def _build(tmp, mutation=None):
     return lib
 
 
-def _pins(lib, test_file, stop_first=True):
-    env = dict(os.environ, ORACLE_LIBRARY=lib, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "4"))
+def _pins(lib, test_file, stop_first=True, threads=None):
+    env = dict(os.environ, ORACLE_LIBRARY=lib,
+               OMP_NUM_THREADS=str(threads) if threads else os.environ.get("OMP_NUM_THREADS", "4"))
     cmd = [sys.executable, "-m", "pytest", test_file, "-q", "-m", "not gpu", "-p", "no:cacheprovider"]
     if stop_first:
         cmd.append("-x")
@@ -109,8 +109,18 @@ def test_unmutated_copy_passes_the_pins(tmp_path):
         assert r.returncode == 0, r.stdout[-2000:]
 
 
-@pytest.mark.parametrize("mid,fname,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_planted_mistake_fails_a_pin(tmp_path, mid, fname, old, new, pins):
-    lib = _build(str(tmp_path), (fname, old, new))
-    r = _pins(lib, pins)
-    assert r.returncode == 1, f"{mid}: no pin in {pins} failed\n{r.stdout[-1500:]}"
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    """All mutations, several at a time (each in its own build and process)."""
+    def run(mutant):
+        mid, fname, old, new, pins = mutant
+        d = tmp_path / mid
+        d.mkdir()
+        lib = _build(str(d), (fname, old, new))
+        return mid, pins, _pins(lib, pins, threads=1)
+
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(run, MUTANTS))
+    missed = [f"{mid} ({pins}): exit {r.returncode}\n{r.stdout[-600:]}" for mid, pins, r in results
+              if r.returncode != 1]
+    assert not missed, "planted mistakes no pin caught:\n" + "\n".join(missed)
