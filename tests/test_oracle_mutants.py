@@ -66,6 +66,12 @@ MUTANTS = [
      CODEC),
     ("codec-half-truncates", "zfp_oracle.c", "return (int32_t)floor((double)a / 2.0);", "return a / 2;", CODEC),
     ("codec-no-plane-raise", "zfp_oracle.c", "if (p == 30 || p == 31) p = 32;", "if (p == 31) p = 32;", CODEC),
+    ("codec-length-table-off-by-one", "zfp_oracle.c", "lengths[b] = (uint16_t)(bw.pos - before);",
+     "lengths[b] = (uint16_t)(bw.pos - before + 1);", CODEC),
+    ("codec-gather-x-y-swapped", "zfp_oracle.c",
+     "      float v[64];\n      zo_gather(in, nx, ny, nz, &L, b, v);",
+     "      float v[64], t[64];\n      zo_gather(in, nx, ny, nz, &L, b, t);\n"
+     "      for (int q = 0; q < 64; q++) v[q] = t[((q >> 2) & 3) + 4 * (q & 3) + 16 * (q >> 4)];", CODEC),
     ("codec-guard-planes", "zfp_oracle.c", "#define ZO_G 11", "#define ZO_G 8", CODEC),
     ("codec-fraction-bits", "zfp_oracle.c", "#define ZO_S 25", "#define ZO_S 24", CODEC),
     ("codec-lifting-trend", "zfp_oracle.c", "  d0 = d0 - zo_half(D);\n  d1 = d1 - zo_half(D);\n  p[0] = S;",
