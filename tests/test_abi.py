@@ -113,3 +113,15 @@ def test_selftest_argument_validation_without_gpu(fwi_lib):
     assert fwi_lib.fwi_selftest_damped_quotient(None, None, None, 4, None) == _lib.FWI_ERR_ARG
     n = C.c_int(-1)
     assert fwi_lib.fwi_ckpt_store_slot_bytes(None, None, 0, C.byref(n)) == _lib.FWI_ERR_ARG
+
+
+def test_python_binding_rejects_bad_tensors_without_gpu():
+    """The binding checks devices, dtypes and shapes before any library call."""
+    import torch
+    from paper_2009_12623_gb300 import api
+    with pytest.raises(ValueError):
+        api.selftest_damped_quotient(torch.ones(3), torch.ones(4))
+    with pytest.raises(TypeError):
+        api.selftest_damped_quotient(torch.ones(3), torch.ones(3))  # host tensors
+    with pytest.raises(TypeError):
+        api.dot_f64(torch.ones(3, dtype=torch.float64), torch.ones(3, dtype=torch.float64))
