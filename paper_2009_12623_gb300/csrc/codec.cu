@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "codec_block.cuh"
 #include "common.cuh"
 
@@ -678,6 +680,28 @@ ZLayout zlayout(int nx, int ny, int nz) {
 }
 
 
+// The codec kernels' dynamic shared-memory limit: a kernel attribute takes
+// effect in the context of the device current when it is set, so it is set
+// once per device, on that device's first launch.
+constexpr int kMaxDevices = 64;
+static std::mutex g_attr_mu;
+static bool g_attr_done[kMaxDevices];
+
+static cudaError_t ensure_codec_attributes() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (g_attr_done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_encode_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmem);
+  if (e != cudaSuccess) return e;
+  g_attr_done[dev] = true;
+  return cudaSuccess;
+}
+
 static EncArgs encode_args(const float* in, Grid g, int minexp, uint8_t* out,
                            const unsigned long long* d_base, size_t capacity,
                            unsigned long long* d_size, int* d_status) {
@@ -727,13 +751,8 @@ cudaError_t zfp_encode_launch(const float* in, Grid g, int minexp, uint8_t* out,
   st.words = reinterpret_cast<unsigned*>(st.offset + a.nchunks);
   cudaError_t e = cudaMemsetAsync(st.tile_sum, 0, ntiles * 8, s);
   if (e != cudaSuccess) return e;
+  if ((e = ensure_codec_attributes()) != cudaSuccess) return e;
   const int ps = prof_begin(KC_ZFP_ENCODE, s);
-  static bool smem_set = false;  // one attribute call per process (same value on every device)
-  if (!smem_set) {
-    e = cudaFuncSetAttribute(k_encode_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
-    if (e != cudaSuccess) return e;
-    smem_set = true;
-  }
   k_encode_stage<<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, kEncSmem, s>>>(a, st);
   k_encode_compact<<<(unsigned)ntiles, 256, 0, s>>>(a, st);
   k_encode_place<<<(unsigned)((a.nchunks + 7) / 8), 256, 0, s>>>(a, st);
@@ -787,12 +806,8 @@ cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_bas
   a.length_table = L.length_table;
   a.payload = L.payload;
   a.status = d_status;
-  static bool smem_set = false;  // one attribute call per process (same value on every device)
-  if (!smem_set) {
-    const cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmem);
-    if (e != cudaSuccess) return e;
-    smem_set = true;
-  }
+  const cudaError_t e = ensure_codec_attributes();
+  if (e != cudaSuccess) return e;
   const int ps = prof_begin(KC_ZFP_DECODE, s);
   k_decode<<<(unsigned)((L.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, kDecSmem, s>>>(a);
   prof_end(ps, s);

@@ -35,8 +35,14 @@
 namespace {
 
 constexpr long kMaxChunks = 131072;
-// descriptors (kMaxChunks), chunk ticket (1), stream size (1), status (1)
+// Word layout of the block for a field of nchunks chunks: words [0, nchunks)
+// hold the chunks' look-back descriptors and word nchunks the chunk ticket
+// (both cleared by the encoder launch); the stream size and the status word
+// sit at fixed offsets after the largest descriptor area.
+constexpr long kSizeWord = kMaxChunks + 2;
+constexpr long kStatusWord = kMaxChunks + 3;
 constexpr long kScratchWords = kMaxChunks + 8;
+static_assert(kStatusWord < kScratchWords, "scratch layout");
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
 
@@ -70,16 +76,21 @@ extern "C" int zfp_compress_fixed_accuracy_noalloc(const float* d_in, int nx, in
   if (!d_in || !d_out || !h_out_bytes || nx <= 0 || ny <= 0 || nz <= 0 || !(atol > 0.0) ||
       !isfinite(atol) || ((uintptr_t)d_out & 7) || ((uintptr_t)d_in & 3))
     return FWI_ERR_ARG;
-  const ZLayout L = zlayout(nx, ny, nz);
-  if (L.nchunks > kMaxChunks) return FWI_ERR_ARG;  // beyond the fixed scratch
+  // size guard in 64-bit arithmetic, before any layout work: each block
+  // count is at most 2^29, so no product below can overflow
+  const long nbx = ((long)nx + 3) / 4, nby = ((long)ny + 3) / 4, nbz = ((long)nz + 3) / 4;
+  const long max_blocks = kMaxChunks * ZC_CHUNK;
+  if (nbx > max_blocks || nby > max_blocks || nbz > max_blocks || nbx * nby > max_blocks ||
+      nbx * nby * nbz > max_blocks)
+    return FWI_ERR_ARG;  // beyond the fixed scratch
   unsigned long long* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) {
     cudaGetLastError();
     return FWI_ERR_CUDA;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  unsigned long long* d_size = scratch + kMaxChunks + 2;
-  int* d_status = reinterpret_cast<int*>(scratch + kMaxChunks + 3);
+  unsigned long long* d_size = scratch + kSizeWord;
+  int* d_status = reinterpret_cast<int*>(scratch + kStatusWord);
   int e_frexp;
   frexp(atol, &e_frexp);
   const int minexp = e_frexp - 1;

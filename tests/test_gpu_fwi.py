@@ -149,10 +149,10 @@ def test_binomial_compressed_tracks_oracle(cuda, oracle):
     w = shot.wavelet.astype(np.float64)
     d_obs = oracle.forward(og, synth.slowness2(shot.v_true).astype(np.float64), w, shot.src, shot.rec)
     g_raw, phi_raw, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs)
-    g_oz, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs, mode=3, k=4, atol=1e-6)
-    g_gz, phi_gz, stats = _grad(cuda, shot, d_obs, 3, k=4, atol=1e-6)
-    e_o, e_g = rel(g_oz, g_raw), rel(g_gz, g_raw)
-    assert e_g <= 1.5 * e_o + TOL, (e_g, e_o)
+    g_oz, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs, mode=3, k=4, atol=1e-4)
+    g_graw, *_ = _grad(cuda, shot, d_obs, 3, k=4)
+    g_gz, phi_gz, stats = _grad(cuda, shot, d_obs, 3, k=4, atol=1e-4)
+    _same_compression_error(g_gz, g_graw, g_oz, g_raw)
     assert stats["used_bytes"] < stats["raw_bytes"] / 2
 
 
@@ -183,11 +183,22 @@ def test_every_k_raw_bitwise_equals_full_history(cuda, two_layer, k):
     assert np.array_equal(g_full, g_k) and phi_full == phi_k
 
 
+def _same_compression_error(g_gz, g_graw, g_oz, g_oraw):
+    """Both sides compress their own (FP32 vs FP64-rounded) checkpoints, so
+    their lossy gradients are two draws of the compression error, not the
+    same numbers.  Each side's error is measured against its own raw-
+    checkpoint gradient, which removes the FP32-vs-FP64 floor (about 1e-6
+    here, above the errors being compared), and the two must agree within a
+    factor of two either way."""
+    e_o, e_g = rel(g_oz, g_oraw), rel(g_gz, g_graw)
+    print(f"compression error: GPU {e_g:.3e}, oracle {e_o:.3e}, ratio {e_g / e_o:.3f}")
+    assert 0.5 <= e_g / e_o <= 2.0, (e_g, e_o)
+    assert rel(g_graw, g_oraw) < TOL
+
+
 def test_compressed_gradient_tracks_oracle(cuda, oracle, two_layer):
-    """Plain checkpointed gradient: every 10 steps, atol = 1e-4.  Both sides
-    compress their own (FP32 vs FP64-rounded) checkpoints, so the lossy
-    gradients differ by about the compression error itself; the GPU error
-    against the uncompressed FP64 gradient must match the oracle's."""
+    """Plain checkpointed gradient: every 10 steps, atol = 1e-4; the GPU's
+    compression error matches the oracle's (two-sided, no additive slack)."""
     from paper_2009_12623_gb300 import synth
     shot, d_obs = two_layer
     og = _og(oracle, shot.geom)
@@ -195,9 +206,9 @@ def test_compressed_gradient_tracks_oracle(cuda, oracle, two_layer):
     w = shot.wavelet.astype(np.float64)
     g_raw, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs)
     g_oz, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs, mode=2, k=10, atol=1e-4)
+    g_graw, *_ = _grad(cuda, shot, d_obs, 2, k=10)
     g_gz, _, stats = _grad(cuda, shot, d_obs, 2, k=10, atol=1e-4)
-    e_o, e_g = rel(g_oz, g_raw), rel(g_gz, g_raw)
-    assert e_g <= 1.5 * e_o + TOL, (e_g, e_o)
+    _same_compression_error(g_gz, g_graw, g_oz, g_raw)
     assert stats["used_bytes"] < stats["raw_bytes"]
 
 

@@ -52,3 +52,32 @@ def test_noalloc_reports_capacity_and_rejects_oversize(cuda, fwi_lib):
     st = fwi_lib.zfp_compress_fixed_accuracy_noalloc(f.data_ptr(), 4096, 4096, 4096, 1e-3, out.data_ptr(),
                                                      64, C.byref(n), torch.cuda.current_stream().cuda_stream)
     assert st == _lib.FWI_ERR_ARG
+
+
+def test_noalloc_bitwise_at_the_largest_accepted_field(cuda, fwi_lib):
+    """At exactly the fixed scratch's limit (131,072 chunks: 1024 x 512 x 512
+    values) the single-pass encoder's look-back runs across many waves of
+    CTAs; its stream must still equal the regular entry point's bit for bit,
+    on two calls in a row.  One chunk row more is refused."""
+    from paper_2009_12623_gb300 import _lib, api
+    nz, ny, nx = 512, 512, 1024
+    gen = torch.Generator(device=cuda)
+    gen.manual_seed(12)
+    z = torch.arange(nz, device=cuda, dtype=torch.float32)[:, None, None]
+    y = torch.arange(ny, device=cuda, dtype=torch.float32)[None, :, None]
+    x = torch.arange(nx, device=cuda, dtype=torch.float32)[None, None, :]
+    # a wave packet over a quiet background: chunk sizes from one bit per block to dense
+    f = torch.sin(0.11 * x + 0.05 * y) * torch.cos(0.07 * z) * torch.exp(-((x - 500) ** 2 + (y - 260) ** 2) / 4e4)
+    f = (f + 1e-3 * torch.randn((nz, ny, nx), device=cuda, generator=gen)).contiguous()
+    cap = api.zfp_max_compressed_bytes(nx, ny, nz)
+    for atol in (1e-4, 1e-2):
+        st0, n0, ref = _call(fwi_lib, "zfp_compress_fixed_accuracy", f, atol, cap)
+        st1, n1, got = _call(fwi_lib, "zfp_compress_fixed_accuracy_noalloc", f, atol, cap)
+        assert st0 == 0 and st1 == 0 and n1 == n0
+        assert torch.equal(got[:n1], ref[:n0])
+        del ref, got
+    n = C.c_size_t(0)
+    out = torch.zeros(64, dtype=torch.uint8, device=cuda)
+    st = fwi_lib.zfp_compress_fixed_accuracy_noalloc(f.data_ptr(), nx + 4, ny, nz, 1e-3, out.data_ptr(), 64,
+                                                     C.byref(n), torch.cuda.current_stream().cuda_stream)
+    assert st == _lib.FWI_ERR_ARG
