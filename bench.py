@@ -11,7 +11,9 @@ imaging -- the whole hot path.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Prints one JSON line (rank 0).  The default run finishes in a few minutes.
+With N GPUs (torchrun) each rank models its own shot and the ranks' gradients
+and misfits are summed (stacking, one all-reduce per step).  Prints one JSON
+line (rank 0).  The default run finishes in a few minutes.
 """
 from __future__ import annotations
 
@@ -47,12 +49,11 @@ def parse():
     p.add_argument("--arena-gb", type=float, default=0.0,
                    help="checkpoint arena size (0 = all free memory minus the working set)")
     p.add_argument("--workload", default="overthrust",
-                   choices=["overthrust", "batch", "fwi", "codec", "tradeoff", "restart"],
+                   choices=["overthrust", "batch", "fwi", "codec", "tradeoff"],
                    help="batch: 32-shot survey, batched plan against one call per shot; "
                         "fwi: 16-shot inversion through autograd, batched against per shot; "
                         "codec: 512^3 shell snapshots, atol sweep; "
-                        "tradeoff: gradient error vs memory for compression, subsampling, binomial; "
-                        "restart: error of a forward run continued from a lossy checkpoint")
+                        "tradeoff: gradient error vs memory for compression, subsampling, binomial")
     p.add_argument("--iters", type=int, default=10, help="fwi workload: descent iterations per path")
     p.add_argument("--shots", type=int, default=32)
     p.add_argument("--ckpt-k", type=int, default=10, help="batch workload: checkpoint pair every K steps")
@@ -88,6 +89,19 @@ def max_over_ranks(pg, x: float) -> float:
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     t = torch.tensor([x], dtype=torch.float64, device=dev)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def stack(pg, grad, phi: float) -> float:
+    """Stacking across ranks (Sec. 2: the misfit and its gradient are sums
+    over shots): every rank ends the step holding the sum of all ranks'
+    shot gradients (in place) and returns the summed misfit."""
+    if pg is None:
+        return phi
+    import torch
+    pg.all_reduce(grad, op=pg.ReduceOp.SUM)
+    t = torch.tensor([phi], dtype=torch.float64, device=grad.device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -220,11 +234,30 @@ def peaks():
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(shot, u_field=None, threads_note=True):
+SAMPLE_STEP = 1200          # the codec sample is the state at this step (2.1 s of 4 s)
+SAMPLE_SLAB = 16            # planes per slab
+_snapshot_cache = {}
+
+
+def sample_planes(g):
+    """Four 16-plane slabs: at the source depth and at 1/3, 1/2 and 2/3 of the
+    depth (never the absorbing layer alone)."""
+    zs = min(g.nbl + 2, g.nz - SAMPLE_SLAB)
+    starts = [zs] + [min(g.nz - SAMPLE_SLAB, max(zs + SAMPLE_SLAB, int(g.nz * q))) for q in (1 / 3, 1 / 2, 2 / 3)]
+    return [list(range(z0, z0 + SAMPLE_SLAB)) for z0 in starts]
+
+
+def oracle_sample(shot, atol):
     """Time the oracle (as it stands) on a bounded sample of the workload and
-    extrapolate to one shot gradient: forward and adjoint steps on the full
-    grid (per-step cost from nt=1 vs nt=2 runs), codec on a 16-plane slab of
-    a propagated wavefield scaled to the full grid."""
+    extrapolate to one shot gradient.  The same function, on the same inputs,
+    serves both the GPU arm's cpu_baseline and the reference arm:
+    * forward and adjoint steps on the full grid, per-step cost from nt = 2
+      minus nt = 1 runs, after one untimed run of each (first touch of the
+      oracle's FP64 fields);
+    * encode + decode at atol of four 16-plane slabs (source depth, 1/3, 1/2
+      and 2/3 of the depth) of the shot's wavefield at step 1200, the seeded
+      analytic snapshot of synth.wavefield_snapshot (direct wave and layer
+      reflections), scaled to the full depth."""
     import numpy as np
     import oracle
     from paper_2009_12623_gb300 import synth
@@ -233,6 +266,13 @@ def oracle_sample(shot, u_field=None, threads_note=True):
     m = synth.slowness2(shot.v0).astype(np.float64)
     w = shot.wavelet.astype(np.float64)
     rec = shot.rec[:64]
+    key = (g.nx, g.ny, g.nz, shot.src)
+    if key not in _snapshot_cache:
+        slabs = sample_planes(g)
+        snap = synth.wavefield_snapshot(shot, SAMPLE_STEP * g.dt, [z for sl in slabs for z in sl])
+        _snapshot_cache[key] = (slabs, [np.ascontiguousarray(snap[i * SAMPLE_SLAB:(i + 1) * SAMPLE_SLAB])
+                                        for i in range(len(slabs))])
+    slabs, fields = _snapshot_cache[key]
 
     def fwd(nt):
         og.nt = nt
@@ -247,26 +287,25 @@ def oracle_sample(shot, u_field=None, threads_note=True):
         oracle.adjoint_trace(og, m, r, rec, shot.src)
         return time.perf_counter() - t
 
+    fwd(1)
+    adj(1)
     t_fwd = max(1e-9, fwd(2) - fwd(1))
     t_adj = max(1e-9, adj(2) - adj(1))
-    slab = 16
-    if u_field is None:
-        rng = np.random.default_rng(0)
-        u_field = rng.normal(size=(slab, g.ny, g.nx)).astype(np.float32) * 0.1
-    sl = np.ascontiguousarray(u_field[:slab], dtype=np.float32)
-    t = time.perf_counter()
-    s = oracle.zfp_compress(sl, 1e-4)
-    t_enc = time.perf_counter() - t
-    t = time.perf_counter()
-    oracle.zfp_decompress(s, sl.shape)
-    t_dec = time.perf_counter() - t
-    scale = g.nz / slab
-    per_step = t_fwd + t_adj + (t_enc + t_dec) * scale
+    t_codec = 0.0
+    for f in fields:
+        t = time.perf_counter()
+        st = oracle.zfp_compress(f, atol)
+        oracle.zfp_decompress(st, f.shape)
+        t_codec += time.perf_counter() - t
+    scale = g.nz / (SAMPLE_SLAB * len(fields))
+    per_step = t_fwd + t_adj + t_codec * scale
     sec_per_gradient = per_step * g.nt
     sample = (f"oracle forward+adjoint step on the full {g.nx}x{g.ny}x{g.nz} grid (per-step time from "
-              f"nt=2 minus nt=1 runs: {t_fwd:.2f} s + {t_adj:.2f} s) and codec encode+decode of a "
-              f"{slab}-plane slab of a propagated wavefield at atol=1e-4 ({t_enc + t_dec:.2f} s, "
-              f"x{scale:.1f} to the full grid), extrapolated to {g.nt} steps")
+              f"nt=2 minus nt=1 runs after a warm-up run: {t_fwd:.2f} s + {t_adj:.2f} s) and codec "
+              f"encode+decode at atol={atol:g} of four {SAMPLE_SLAB}-plane slabs starting at z = "
+              f"{', '.join(str(sl[0]) for sl in slabs)} (source depth, 1/3, 1/2, 2/3 of the depth) of the "
+              f"shot's wavefield at step {SAMPLE_STEP} (seeded analytic snapshot: direct wave and layer "
+              f"reflections), {t_codec:.2f} s, x{scale:.2f} to the full depth; extrapolated to {g.nt} steps")
     return 1.0 / sec_per_gradient, oracle.num_threads(), sample, per_step
 
 
@@ -277,13 +316,13 @@ def run_reference(args):
         return
     shot, _ = workload(args, 0)
     for _ in range(args.warmup):
-        oracle_sample(shot)
+        oracle_sample(shot, args.atol)
     vals = []
     t0 = time.perf_counter()
     cores = None
     sample = None
     for _ in range(args.steps):
-        v, cores, sample, _ = oracle_sample(shot)
+        v, cores, sample, _ = oracle_sample(shot, args.atol)
         vals.append(v)
     wall = time.perf_counter() - t0
     value = statistics.mean(vals)
@@ -335,8 +374,9 @@ def run_fwi(args):
 
     def step():
         grad.zero_()
-        return api.gradient(g, m0, w, shot.src, rec, d_obs, store, mode=policy_mode, k=policy_k,
-                            atol=args.atol, grad=grad)
+        _, phi = api.gradient(g, m0, w, shot.src, rec, d_obs, store, mode=policy_mode, k=policy_k,
+                              atol=args.atol, grad=grad)
+        return grad, stack(pg, grad, phi)
 
     try:
         step()
@@ -421,8 +461,13 @@ def run_fwi(args):
 
         def hstep():
             h_grad.zero_()
-            return api.gradient_host(g, h_m, w, shot.src, h_rec, h_obs, store, mode=policy_mode,
-                                     k=policy_k, atol=args.atol, grad=h_grad)
+            _, phi = api.gradient_host(g, h_m, w, shot.src, h_rec, h_obs, store, mode=policy_mode,
+                                       k=policy_k, atol=args.atol, grad=h_grad)
+            if pg is not None:  # stack the host gradients through the device
+                dg = h_grad.to(dev, non_blocking=True)
+                phi = stack(pg, dg, phi)
+                h_grad.copy_(dg)
+            return h_grad, phi
         hstep()
         barrier(pg)
         t0 = time.perf_counter()
@@ -433,14 +478,15 @@ def run_fwi(args):
         t_e2e = max_over_ranks(pg, time.perf_counter() - t0)
         e2e = {"value": ws * args.steps / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": int(h_m.numel() * 4 + h_obs.numel() * 4 + h_rec.numel() * 4 +
-                                         h_grad.numel() * 4 + g.nt * 4),
-               "d2h_bytes_per_step": int(h_grad.numel() * 4 + 8),
+                                         h_grad.numel() * 4 * (2 if ws > 1 else 1) + g.nt * 4),
+               "d2h_bytes_per_step": int(h_grad.numel() * 4 * (2 if ws > 1 else 1) + 8),
                "entry_point": "fwi_gradient_host (pinned host buffers)"}
 
     # ---- gradient error at this tolerance vs raw (uncompressed) checkpoints ----
     # (after the timed region; the compressed store is released first so the
     # raw pairs and the recompute ring fit)
     verify = None
+    plain_k = None
     if not args.no_verify:
         g_lossy = grad.clone()
         store.close()
@@ -450,14 +496,29 @@ def run_fwi(args):
         vstore = api.CheckpointStore(max(1 << 30, free - K * cells * 4 - 24 * (1 << 30)))
         grad.zero_()
         try:
-            api.gradient(g, m0, w, shot.src, rec, d_obs_v, vstore, mode=api.FWI_CKPT_EVERY_K, k=K,
-                         atol=0.0, grad=grad)
+            ev_a = torch.cuda.Event(enable_timing=True)
+            ev_b = torch.cuda.Event(enable_timing=True)
+            for rep in range(2):   # the first run sets up the recompute ring
+                grad.zero_()
+                ev_a.record()
+                api.gradient(g, m0, w, shot.src, rec, d_obs_v, vstore, mode=api.FWI_CKPT_EVERY_K, k=K,
+                             atol=0.0, grad=grad)
+                ev_b.record()
+            torch.cuda.synchronize()
             num = api.dot_f64(g_lossy - grad, g_lossy - grad)
             den = api.dot_f64(grad, grad)
             cos = api.dot_f64(g_lossy, grad) / np.sqrt(api.dot_f64(g_lossy, g_lossy) * den)
             verify = {"rel_l2_vs_raw_checkpoints": float(np.sqrt(num / den)),
                       "angle_rad": float(np.arccos(min(1.0, cos))),
                       "reference": f"same sweeps with raw FP32 checkpoint pairs every {K} steps"}
+            # The paper's trade-off (Sec. 5): compression pays only where it beats recomputation.
+            # The exact alternative: raw pairs every K steps, segments recomputed into a K-field ring.
+            pairs = vstore.stats()["used_bytes"]
+            ring = K * 4 * g.ny * g.nz * (-(-g.nx // 4) * 4)
+            plain_k = {"k": K, "s_per_gradient": round(ev_a.elapsed_time(ev_b) / 1e3, 3),
+                       "GiB_held": round((pairs + ring) / 2**30, 1),
+                       "note": "second of two runs after the timed region (CUDA events); GiB = raw pairs + "
+                               "recompute ring"}
         except api.FwiError as e:
             verify = {"error": str(e)}
         vstore.close()
@@ -465,14 +526,7 @@ def run_fwi(args):
     # ---- CPU oracle baseline (rank 0, N=1) ------------------------------------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        slab = None
-        try:
-            gg = api.Geometry(**{**g.__dict__, "nt": min(g.nt, 1200)})
-            _, _, ul = api.forward(gg, m0, w, shot.src, rec[:1], return_state=True)
-            slab = ul[:16].cpu().numpy()
-        except Exception:
-            slab = None
-        v, cores, sample, _ = oracle_sample(shot, slab)
+        v, cores, sample, _ = oracle_sample(shot, args.atol)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -486,7 +540,10 @@ def run_fwi(args):
                                      "compression_factor": round(stats["raw_bytes"] / max(1, stats["used_bytes"]), 2),
                                      "checkpoints": stats["n_checkpoints"],
                                      "cf_by_tenth_of_run": cf_tenths},
-                "misfit": phi, "gradient_error": verify}
+                "misfit": phi, "gradient_error": verify,
+                "lossy_full_history": {"s_per_gradient": round(ms_max / args.steps / 1e3, 3),
+                                       "GiB_held": round(stats["used_bytes"] / 2**30, 1)},
+                "plain_every_k_raw": plain_k}
         print(json.dumps(line), flush=True)
     store.close()
     if pg is not None:
@@ -851,66 +908,6 @@ def run_tradeoff(args):
         print(json.dumps(line), flush=True)
 
 
-def run_restart(args):
-    """The forward-propagation experiment of Sec. 4 on the Overthrust-shaped
-    grid (881 x 881 x 287, dt = 1.75 ms, 8 Hz): run 550 steps, compress the
-    state pair (u^549, u^550) at atol, continue 550 more steps from the lossy
-    and from the exact pair, and record the L_inf and L2 norms of the
-    difference of the two runs (FP64 reductions on the GPU) after every step
-    for the first 10 steps, then every 10 steps."""
-    import numpy as np
-    import torch
-    ws, rank, local, pg = dist_setup(args)
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA GPU (the product path has no CPU fallback)")
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2009_12623_gb300 import api, synth
-    t1, t2 = 550, 550
-    shot = synth.overthrust_like_shot(nt=t1 + t2)
-    g = shot.geom
-    m = torch.from_numpy(synth.slowness2(shot.v0)).to(dev)
-    rec = torch.from_numpy(shot.rec[:1]).to(dev)
-    w = shot.wavelet
-    geo = lambda nt: api.Geometry(**{**g.__dict__, "nt": nt})  # noqa: E731
-    _, up, uc = api.forward(geo(t1), m, w[:t1], shot.src, rec, return_state=True)
-    marks = list(range(1, 11)) + list(range(20, t2 + 1, 10))
-    runs = []
-    for atol in (1e-6, 1e-4):
-        exact = [up.clone(), uc.clone()]
-        streams = [api.zfp_compress(f, atol) for f in exact]
-        lossy = [api.zfp_decompress(s_, f.shape) for s_, f in zip(streams, exact)]
-        cf = 2 * exact[0].numel() * 4 / sum(int(s_.numel()) for s_ in streams)
-        e0 = float((lossy[1] - exact[1]).abs().max())
-        done, curve = 0, []
-        for n in marks:
-            k = n - done
-            wk = w[t1 + done:t1 + n]
-            _, a0, a1 = api.forward(geo(k), m, wk, shot.src, rec, u_prev_init=exact[0], u_cur_init=exact[1],
-                                    return_state=True)
-            _, b0, b1 = api.forward(geo(k), m, wk, shot.src, rec, u_prev_init=lossy[0], u_cur_init=lossy[1],
-                                    return_state=True)
-            exact, lossy, done = [a0, a1], [b0, b1], n
-            d = a1 - b1
-            curve.append({"steps": n, "linf": float(d.abs().max()), "l2": float(np.sqrt(api.dot_f64(d, d))),
-                          "field_linf": float(a1.abs().max())})
-        l2 = [c["l2"] for c in curve]
-        runs.append({"atol": atol, "checkpoint_cf": cf, "restart_linf": e0, "peak_l2_at_step": marks[int(np.argmax(l2))],
-                     "final_over_peak_l2": l2[-1] / max(l2), "max_linf_over_atol": max(c["linf"] for c in curve) / atol,
-                     "curve": curve})
-        del exact, lossy, streams
-    line = {"metric": "error of a forward run restarted from a lossy checkpoint", "value": None, "unit": None,
-            "n_gpus": ws, "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": None, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"overthrust-like {g.nx}x{g.ny}x{g.nz} at {g.h:.0f} m, dt={g.dt * 1e3:.2f} ms, "
-                                   f"8 Hz; {t1} steps, state pair compressed, {t2} steps continued"},
-            "restart": runs}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-
-
 def main():
     args = parse()
     if args.impl == "reference":
@@ -923,8 +920,6 @@ def main():
         run_codec(args)
     elif args.workload == "tradeoff":
         run_tradeoff(args)
-    elif args.workload == "restart":
-        run_restart(args)
     else:
         run_fwi(args)
 

@@ -160,6 +160,40 @@ def overthrust_like_shot(nx: int = 881, ny: int = 881, nz: int = 287, nt: int = 
     return Shot("overthrust_like", geom, f, (int(sx), int(sy), zr), rec, v_true, v0)
 
 
+def wavefield_snapshot(shot: Shot, t: float, planes) -> np.ndarray:
+    """Analytic stand-in for the shot's wavefield at time t on the given
+    z-planes (float32, (len(planes), ny, nx)): the direct wave and the
+    reflections from every layer interface of the velocity column under the
+    source, each a spherical Ricker front h^3 q(t - r/c) / (4 pi r) from the
+    source or its mirror image across the interface (amplitude scaled by the
+    normal-incidence reflection coefficient, speed the mean velocity above
+    the interface).  A seeded, reproducible input shaped like a propagated
+    state, for timing the codec on the same data anywhere."""
+    g = shot.geom
+    sx, sy, sz = shot.src
+    col = shot.v_true[:, sy, sx].astype(np.float64)
+    fronts = [(float(sz), float(col[sz]), 1.0)]
+    for zk in np.nonzero(np.diff(col))[0] + 1:
+        if zk <= sz:
+            continue
+        r = (col[zk] - col[zk - 1]) / (col[zk] + col[zk - 1])
+        fronts.append((2.0 * zk - sz, float(col[sz:zk].mean()), float(r)))
+    x = (np.arange(g.nx) - sx)[None, :] * g.h
+    y = (np.arange(g.ny) - sy)[:, None] * g.h
+    rxy2 = x * x + y * y
+    t0 = 1.5 / shot.f
+    out = np.zeros((len(planes), g.ny, g.nx), np.float32)
+    for i, z in enumerate(planes):
+        acc = np.zeros(g.ny * g.nx)
+        for zi, c, a in fronts:
+            r = np.sqrt(rxy2 + ((z - zi) * g.h) ** 2).ravel()
+            near = np.nonzero(np.abs(t - r / c - t0) < 3.0 / shot.f)[0]   # the front's support
+            rr = r[near]
+            acc[near] += a * g.h ** 3 / (4 * np.pi * np.maximum(rr, g.h)) * ricker(t - rr / c, shot.f, t0)
+        out[i] = acc.reshape(g.ny, g.nx)
+    return out
+
+
 def shells_field(n: int = 512, seed: int = 0, nshell: int = 8, f: float = 15.0, h: float = 10.0,
                  c: float = 1500.0, rmin: float = 50.0, rmax: float = 200.0,
                  noise: float = 1e-7) -> np.ndarray:
