@@ -510,6 +510,7 @@ struct DecArgs {
   long nbx, nby, nblocks, nchunks;
   unsigned long long chunk_table, length_table, payload;
   int* status;
+  bool skip_zero;  // leave blocks coded as zero unwritten
 };
 
 // Bit reader over a chunk's words (staged in shared memory, or in global
@@ -621,6 +622,7 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(
     atomicOr(a.status, ST_CORRUPT);
     return;
   }
+  if (a.skip_zero && planes == 0) return;  // a zero block: its consumers skip it
   float v[64];
   {
     uint32_t u[64];
@@ -784,8 +786,21 @@ cudaError_t zfp_encode_chained_launch(const float* in, Grid g, int minexp, uint8
   return cudaGetLastError();
 }
 
+ZeroBlocks zero_blocks(const uint8_t* arena, const unsigned long long* base, size_t capacity, Grid g) {
+  const ZLayout L = zlayout(g.nx, g.ny, g.nz);
+  ZeroBlocks z;
+  z.arena = arena;
+  z.base = base;
+  z.length_table = L.length_table;
+  z.payload = L.payload;
+  z.capacity = capacity;
+  z.nbx = (int)L.nbx;
+  z.nby = (int)L.nby;
+  return z;
+}
+
 cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_base, size_t avail,
-                              float* out, Grid g, int* d_status, cudaStream_t s) {
+                              float* out, Grid g, int* d_status, cudaStream_t s, bool skip_zero) {
   ZLayout L = zlayout(g.nx, g.ny, g.nz);
   DecArgs a;
   a.in = in;
@@ -806,6 +821,7 @@ cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_bas
   a.length_table = L.length_table;
   a.payload = L.payload;
   a.status = d_status;
+  a.skip_zero = skip_zero;
   const cudaError_t e = ensure_codec_attributes();
   if (e != cudaSuccess) return e;
   const int ps = prof_begin(KC_ZFP_DECODE, s);

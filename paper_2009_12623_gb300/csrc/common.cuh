@@ -85,9 +85,41 @@ cudaError_t zfp_encode_chained_launch(const float* in, Grid g, int minexp, uint8
 
 // Decompress a stream located at in + *d_base (d_base NULL = 0) of at most
 // `avail` bytes into a pitched field.  Asynchronous; errors go to *d_status.
+// With skip_zero, blocks the stream codes as zero (the single bit 0) are not
+// written: the caller's consumers must then skip them (see ZeroBlocks).
 cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_base,
                               size_t avail, float* out, Grid g, int* d_status,
-                              cudaStream_t s);
+                              cudaStream_t s, bool skip_zero = false);
+
+// Where a compressed field's block-length table lies, for kernels that
+// consume the field decoded with skip_zero: a block whose coded length is one
+// bit decodes to exactly 0, so its cells are neither read nor needed.  The
+// stream starts at arena + *base (a device word); arena == NULL means "no
+// table: every block is live".
+struct ZeroBlocks {
+  const uint8_t* arena;
+  const unsigned long long* base;
+  unsigned long long length_table;  // byte offsets within the stream
+  unsigned long long payload;
+  unsigned long long capacity;      // bytes readable from arena
+  int nbx, nby;                     // blocks per row and per column of a layer
+};
+ZeroBlocks zero_blocks(const uint8_t* arena, const unsigned long long* base, size_t capacity, Grid g);
+
+#ifdef __CUDACC__
+// The length table, or NULL when there is none or the stream does not fit
+// the arena (then every block counts as live).
+__device__ __forceinline__ const uint16_t* zero_table(const ZeroBlocks& z) {
+  if (!z.arena) return nullptr;
+  const unsigned long long b = *z.base;
+  if (b > z.capacity || z.payload > z.capacity - b) return nullptr;
+  return reinterpret_cast<const uint16_t*>(z.arena + b + z.length_table);
+}
+// Whether cell (x, y, z) lies in a block that is not coded as zero.
+__device__ __forceinline__ bool block_live(const uint16_t* tab, const ZeroBlocks& z, int x, int y, int zz) {
+  return !tab || tab[((long)(zz >> 2) * z.nby + (y >> 2)) * z.nbx + (x >> 2)] != 1;
+}
+#endif
 
 // ---- stencil ----------------------------------------------------------------
 struct StencilParams {
@@ -109,13 +141,16 @@ cudaError_t stencil_step_launch(const StencilParams& p, const float* cur, const 
 // Adjoint step with fused imaging:
 //   out = step(cur, prev);  grad -= weight * uk * (out - 2 cur + prev) / dt^2
 // (receiver injection is added afterwards by inject_adjoint_launch).
+// With zb (nullable), blocks of uk that zb marks as zero are not read and
+// their grad cells are left as they are (the imaging term there is exactly 0).
 cudaError_t stencil_adjoint_launch(const StencilParams& p, const float* cur, const float* prev,
                                    float* out, const float* uk, float* grad, float weight,
-                                   cudaStream_t s);
-// out[rec] += r * fac; if uk: grad[rec] -= weight * uk[rec] * r * fac / dt^2.
+                                   cudaStream_t s, const ZeroBlocks* zb = nullptr);
+// out[rec] += r * fac; if uk: grad[rec] -= weight * uk[rec] * r * fac / dt^2
+// (skipped where zb, nullable, marks the block of uk as zero).
 cudaError_t inject_adjoint_launch(const StencilParams& p, const long* rec_cell, const float* rec_fac,
                                   int nrec, const float* resid_row, float* out, const float* uk,
-                                  float* grad, float weight, cudaStream_t s);
+                                  float* grad, float weight, cudaStream_t s, const ZeroBlocks* zb = nullptr);
 // fac[r] = b / (1 + s dt/2) at receiver r (injection weight).
 cudaError_t rec_fac_launch(const StencilParams& p, const long* rec_cell, int nrec, float* fac,
                            cudaStream_t s);

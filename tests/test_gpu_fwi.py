@@ -386,3 +386,19 @@ def test_slot_bytes_report_each_checkpoint(cuda, two_layer):
         api.gradient(g, m, shot.wavelet, shot.src, rec, obs, st, mode=api.FWI_CKPT_EVERY_K, k=10, atol=1e-4)
         b10 = st.slot_bytes()
         assert b10.size == st.stats()["n_checkpoints"] and b10.size % 2 == 0 and b10.size <= 2 * (g.nt // 10 + 1)
+
+
+@pytest.mark.parametrize("which,atol", [("two_layer", 1e-4), ("two_layer", 1e-2), ("ragged", 1e-5)])
+def test_zero_block_skipping_is_exact(cuda, two_layer, which, atol):
+    """The full-history reverse sweep leaves the blocks a compressed state codes
+    as zero undecoded and skips u^k and g there (the imaging term is exactly 0).
+    Every-1 checkpoint pairs decode the very same streams in full, so the two
+    gradients must agree bit for bit; the early, sparse states of these shots
+    are mostly zero blocks."""
+    from paper_2009_12623_gb300 import synth
+    shot, d_obs = two_layer if which == "two_layer" else (_small_shot(), None)
+    if d_obs is None:
+        d_obs = np.zeros((shot.geom.nt, len(shot.rec)))
+    g_full, phi_full, _ = _grad(cuda, shot, d_obs, 1, atol=atol)
+    g_k1, phi_k1, _ = _grad(cuda, shot, d_obs, 2, k=1, atol=atol)
+    assert np.array_equal(g_full.view(np.uint32), g_k1.view(np.uint32)) and phi_full == phi_k1
