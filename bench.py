@@ -191,13 +191,16 @@ def config_dict(args, shot, policy):
 IN_ORDER = ("stencil_forward", "stencil_adjoint_imaging", "zfp_decode")
 
 
-def kernel_bytes(cells, enc_bytes_per_launch):
-    """Algorithmic bytes per launch (halos and scratch excluded)."""
+def kernel_bytes(cells, enc_bytes_per_launch, live=1.0):
+    """Algorithmic bytes per launch (halos and scratch excluded).  `live` is
+    the mean fraction of each stored state's blocks that are not coded as
+    zero: the full-history reverse sweep neither writes (decoder) nor reads
+    u^k and g (adjoint) in the others."""
     return {
         "stencil_forward": 16.0 * cells,                 # read u^n, u^{n-1}, m; write u^{n+1}
-        "stencil_adjoint_imaging": 28.0 * cells,         # + read u^k, read/write g
+        "stencil_adjoint_imaging": (16.0 + 12.0 * live) * cells,  # + read u^k, read/write g where live
         "zfp_encode": 4.0 * cells + enc_bytes_per_launch,
-        "zfp_decode": 4.0 * cells + enc_bytes_per_launch,
+        "zfp_decode": 4.0 * live * cells + enc_bytes_per_launch,
     }
 
 
@@ -424,7 +427,10 @@ def run_fwi(args):
     # ---- roofline of the dominant kernel ---------------------------------------
     pk, peak_kind = peaks()
     enc_bytes = stats["used_bytes"] / max(1, stats["n_checkpoints"])
-    kb = kernel_bytes(cells, enc_bytes)
+    nblocks = -(-g.nx // 4) * -(-g.ny // 4) * -(-g.nz // 4)
+    zero_blocks = store.slot_zero_blocks().astype(np.float64)
+    live = float(1.0 - zero_blocks.mean() / nblocks) if policy_mode == api.FWI_CKPT_FULL and args.atol > 0 else 1.0
+    kb = kernel_bytes(cells, enc_bytes, live)
     timed = {k: v for k, v in prof.items() if k in kb and v[1] > 0}
     # The dominant kernel is the one with the most device time among those that run alone, in
     # order, on the sweep's stream.  The encoder runs on a second stream beside the next forward
@@ -536,7 +542,8 @@ def run_fwi(args):
                 "config": config_dict(args, shot, policy), "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                 "kernels": kernels,
-                "checkpoint_store": {"used_GiB": round(stats["used_bytes"] / 2**30, 2),
+                "checkpoint_store": {"live_block_fraction": round(live, 4),
+                                     "used_GiB": round(stats["used_bytes"] / 2**30, 2),
                                      "compression_factor": round(stats["raw_bytes"] / max(1, stats["used_bytes"]), 2),
                                      "checkpoints": stats["n_checkpoints"],
                                      "cf_by_tenth_of_run": cf_tenths},

@@ -132,6 +132,17 @@ int fwi_ckpt_store_stats(const fwi_ckpt_store* st, fwi_store_stats* out);
  * with cap > 0. */
 int fwi_ckpt_store_slot_bytes(const fwi_ckpt_store* st, unsigned long long* h_bytes, int cap, int* n_out);
 
+/* Blocks of 4x4x4 values that each compressed slot of the last forward sweep
+ * codes as zero (the single bit 0: every value of the block lies below the
+ * tolerance's last coded bit plane, Sec. 1.4), same slot order and argument
+ * rules as fwi_ckpt_store_slot_bytes; raw stores report 0.  Such blocks
+ * decode to exactly 0, and the full-history reverse sweep neither writes nor
+ * images them, so this is how much of each state that sweep skips.  Counted
+ * on the device from the streams' length tables; synchronous.  A slot whose
+ * stream does not fit the arena reports UINT64_MAX. */
+int fwi_ckpt_store_slot_zero_blocks(const fwi_ckpt_store* st, unsigned long long* h_counts, int cap,
+                                    int* n_out);
+
 /* ---- forward modelling (Sec. 2, Eq. (1)-(2)) ------------------------------ */
 /* Runs u^{n+1} for n = 0..nt-1 from the zero state (or from the given pair
  * d_u_prev_init = u^{-1}, d_u_cur_init = u^0) and records

@@ -21,7 +21,7 @@ FWI_ACT_ADVANCE, FWI_ACT_STORE, FWI_ACT_RESTORE, FWI_ACT_RECOMPUTE, FWI_ACT_ADJO
 #: every symbol include/fwi.h declares
 EXPORTS = [
     "fwi_ckpt_schedule", "fwi_ckpt_store_create", "fwi_ckpt_store_destroy", "fwi_ckpt_store_stats",
-    "fwi_ckpt_store_slot_bytes",
+    "fwi_ckpt_store_slot_bytes", "fwi_ckpt_store_slot_zero_blocks",
     "fwi_forward", "fwi_gradient", "fwi_gradient_host", "zfp_max_compressed_bytes",
     "zfp_compress_fixed_accuracy", "zfp_decompress", "fwi_misfit", "fwi_dot_f64",
     "fwi_status_string", "fwi_kernel_launch_count", "fwi_profile_enable", "fwi_profile_reset",
@@ -95,6 +95,7 @@ def load() -> C.CDLL:
         L.fwi_ckpt_store_destroy.argtypes = [vp]
         L.fwi_ckpt_store_stats.argtypes = [vp, C.POINTER(StoreStats)]
         L.fwi_ckpt_store_slot_bytes.argtypes = [vp, C.POINTER(C.c_ulonglong), C.c_int, C.POINTER(C.c_int)]
+        L.fwi_ckpt_store_slot_zero_blocks.argtypes = L.fwi_ckpt_store_slot_bytes.argtypes
         L.fwi_forward.argtypes = [gp, fp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, fp,
                                   fp, fp, fp, fp, vp]
         L.fwi_gradient.argtypes = [gp, fp, vp, C.c_int, C.c_int, C.c_int, ip, C.c_int, fp, fp, dp,

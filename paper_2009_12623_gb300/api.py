@@ -126,6 +126,18 @@ class CheckpointStore:
             self.handle, out.ctypes.data_as(C.POINTER(C.c_ulonglong)), n.value, C.byref(n)))
         return out[:n.value]
 
+    def slot_zero_blocks(self) -> np.ndarray:
+        """fwi_ckpt_store_slot_zero_blocks: blocks each compressed slot codes as
+        zero (decoded exactly 0, skipped by the full-history reverse sweep)."""
+        L = _lib.load()
+        n = C.c_int(0)
+        check("fwi_ckpt_store_slot_zero_blocks",
+              L.fwi_ckpt_store_slot_zero_blocks(self.handle, None, 0, C.byref(n)))
+        out = np.zeros(max(1, n.value), dtype=np.uint64)
+        check("fwi_ckpt_store_slot_zero_blocks", L.fwi_ckpt_store_slot_zero_blocks(
+            self.handle, out.ctypes.data_as(C.POINTER(C.c_ulonglong)), n.value, C.byref(n)))
+        return out[:n.value]
+
     def close(self):
         if self._h:
             _lib.load().fwi_ckpt_store_destroy(self._h)

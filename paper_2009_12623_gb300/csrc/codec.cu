@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "codec_block.cuh"
@@ -659,7 +660,44 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(
   }
 }
 
+// Blocks coded as zero (length one bit) per slot: grid (ctas per slot, slots).
+__global__ void __launch_bounds__(256) k_count_zero_blocks(const uint8_t* arena, const unsigned long long* offs,
+                                                           unsigned long long capacity,
+                                                           unsigned long long length_table,
+                                                           unsigned long long payload, long nblocks,
+                                                           unsigned long long* counts) {
+  const int slot = blockIdx.y;
+  const unsigned long long base = offs[slot];
+  if (base > capacity || payload > capacity - base) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[slot] = ~0ull;
+    return;
+  }
+  const uint16_t* len = reinterpret_cast<const uint16_t*>(arena + base + length_table);
+  unsigned long long n = 0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nblocks; i += (long)gridDim.x * blockDim.x)
+    n += len[i] == 1;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0 && n) atomicAdd(&counts[slot], n);
+}
+
 }  // namespace
+
+cudaError_t zfp_count_zero_blocks_launch(const uint8_t* arena, const unsigned long long* offs, int nslots,
+                                         size_t capacity, Grid g, unsigned long long* counts, cudaStream_t s) {
+  if (nslots <= 0) return cudaSuccess;
+  const ZLayout L = zlayout(g.nx, g.ny, g.nz);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * (size_t)nslots, s);
+  if (e != cudaSuccess) return e;
+  const long per = std::min<long>(64, (L.nblocks + 255) / 256);
+  for (int j0 = 0; j0 < nslots; j0 += 65535) {
+    const int n = std::min(65535, nslots - j0);
+    k_count_zero_blocks<<<dim3((unsigned)per, (unsigned)n), 256, 0, s>>>(
+        arena, offs + j0, capacity, L.length_table, L.payload, L.nblocks, counts + j0);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
 
 ZLayout zlayout(int nx, int ny, int nz) {
   ZLayout L{};

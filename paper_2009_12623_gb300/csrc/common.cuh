@@ -105,6 +105,10 @@ struct ZeroBlocks {
   int nbx, nby;                     // blocks per row and per column of a layer
 };
 ZeroBlocks zero_blocks(const uint8_t* arena, const unsigned long long* base, size_t capacity, Grid g);
+// counts[j] = blocks coded as zero in the stream at arena + offs[j], j < nslots
+// (UINT64_MAX where the stream does not fit the capacity).  Asynchronous.
+cudaError_t zfp_count_zero_blocks_launch(const uint8_t* arena, const unsigned long long* offs, int nslots,
+                                         size_t capacity, Grid g, unsigned long long* counts, cudaStream_t s);
 
 #ifdef __CUDACC__
 // The length table, or NULL when there is none or the stream does not fit

@@ -427,6 +427,36 @@ int fwi_ckpt_store_slot_bytes(const fwi_ckpt_store* st, unsigned long long* h_by
   return FWI_OK;
 }
 
+int fwi_ckpt_store_slot_zero_blocks(const fwi_ckpt_store* st, unsigned long long* h_counts, int cap,
+                                    int* n_out) {
+  if (!st || !n_out || cap < 0 || (cap > 0 && !h_counts)) return FWI_ERR_ARG;
+  const int n = st->filled ? st->nslots : 0;
+  *n_out = n;
+  const int k = std::min(n, cap);
+  if (k == 0) return FWI_OK;
+  if (!st->lossy) {
+    for (int i = 0; i < k; ++i) h_counts[i] = 0;
+    return FWI_OK;
+  }
+  if (!st->d_offs || st->slot_cap < n) return FWI_ERR_CUDA;
+  const Grid G{st->geom.nx, st->geom.ny, st->geom.nz, round_up(st->geom.nx, 4)};
+  unsigned long long* d_counts = nullptr;
+  const size_t bytes = sizeof(unsigned long long) * (size_t)k;
+  if (cudaMalloc(&d_counts, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return FWI_ERR_NOMEM;
+  }
+  const bool ok = zfp_count_zero_blocks_launch(st->arena, st->d_offs, k, st->capacity, G, d_counts, 0) ==
+                      cudaSuccess &&
+                  cudaMemcpy(h_counts, d_counts, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaFree(d_counts);
+  if (!ok) {
+    cudaGetLastError();
+    return FWI_ERR_CUDA;
+  }
+  return FWI_OK;
+}
+
 int fwi_forward(const fwi_geometry* g, const float* d_m, const float* h_wavelet, int src_i,
                 int src_j, int src_k, const int* d_rec_ijk, int nrec, float* d_rec_out,
                 const float* d_u_prev_init, const float* d_u_cur_init, float* d_u_prev_out,

@@ -402,3 +402,32 @@ def test_zero_block_skipping_is_exact(cuda, two_layer, which, atol):
     g_full, phi_full, _ = _grad(cuda, shot, d_obs, 1, atol=atol)
     g_k1, phi_k1, _ = _grad(cuda, shot, d_obs, 2, k=1, atol=atol)
     assert np.array_equal(g_full.view(np.uint32), g_k1.view(np.uint32)) and phi_full == phi_k1
+
+
+def test_slot_zero_blocks_match_the_oracle_streams(cuda, oracle, two_layer):
+    """fwi_ckpt_store_slot_zero_blocks: per stored state, the blocks coded as
+    the single bit 0, equal to the count in the oracle's stream of the same
+    FP32 state (read from its u16 length table); raw stores report 0."""
+    import struct
+    from paper_2009_12623_gb300 import api, synth
+    shot, d_obs = two_layer
+    g = shot.geom
+    m = _dev(cuda, synth.slowness2(shot.v0))
+    rec = _dev(cuda, shot.rec)
+    obs = _dev(cuda, np.asarray(d_obs, np.float32))
+    atol = 1e-4
+    with api.CheckpointStore(1 << 30) as st:
+        api.gradient(g, m, shot.wavelet, shot.src, rec, obs, st, mode=api.FWI_CKPT_FULL, atol=atol)
+        z = st.slot_zero_blocks().astype(np.int64)
+        assert z.size == g.nt
+        for k in (1, 20, 90, g.nt):
+            gk = api.Geometry(**{**g.__dict__, "nt": k})
+            _, _, uk = api.forward(gk, m, shot.wavelet[:k], shot.src, rec, return_state=True)
+            s = oracle.zfp_compress(uk.cpu().numpy(), atol)
+            nblocks, = struct.unpack_from("<Q", s, 24)
+            nchunks, = struct.unpack_from("<I", s, 36)
+            lens = np.frombuffer(s, np.uint16, nblocks, 64 + 8 * nchunks)
+            assert z[k - 1] == int((lens == 1).sum()), k
+        assert z[0] > z[-1] > 0
+        api.gradient(g, m, shot.wavelet, shot.src, rec, obs, st, mode=api.FWI_CKPT_FULL, atol=0.0)
+        assert np.all(st.slot_zero_blocks() == 0)
