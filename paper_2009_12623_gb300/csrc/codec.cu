@@ -117,6 +117,8 @@ struct EncArgs {
   int* status;
   unsigned long long* desc;
   unsigned int* ticket;
+  const uint16_t* live;  // liveness map of the field (NULL = read every block)
+  int live_ntx;
 };
 
 __device__ __forceinline__ void put_u32(uint8_t* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
@@ -285,9 +287,7 @@ struct StageArgs {
   unsigned long long* offset;    // per-chunk word offset in the payload
 };
 
-__device__ __forceinline__ void gather_block(const EncArgs& a, long blk, uint32_t* u) {
-  long bx, by, bz;
-  block_xyz(blk, a.nbx, a.nby, a.nblocks, bx, by, bz);
+__device__ __forceinline__ void gather_block(const EncArgs& a, long bx, long by, long bz, uint32_t* u) {
   const long xb = 4 * bx;
   const bool vec = a.vec_ok && xb + 3 < a.nx;  // 16-byte row loads when aligned and in range
 #pragma unroll
@@ -341,9 +341,14 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_ENC_MIN_CTAS) k_encode_
   const long blk = chunk * ZC_CHUNK + lane;
   const bool valid = blk < a.nblocks;
   int planes = 0, emax = 0, nbits = 0;
-  if (valid) {
+  long bx = 0, by = 0, bz = 0;
+  if (valid) block_xyz(blk, a.nbx, a.nby, a.nblocks, bx, by, bz);
+  // a block the forward step found below the threshold of this tolerance
+  // codes as zero (no coded plane): it is not read
+  const bool read = valid && (!a.live || ((a.live[(bz * a.nby + by) * a.live_ntx + (bx >> 4)] >> (bx & 15)) & 1));
+  if (read) {
     uint32_t u[64];
-    gather_block(a, blk, u);
+    gather_block(a, bx, by, bz, u);
     if (!quantise_coeffs(u, a.minexp, emax, planes)) atomicOr(a.status, ST_NONFINITE);
     if (planes) {  // a block with no coded plane is the single bit 0: nothing to transpose
       transpose32(u);
@@ -563,36 +568,37 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(
   const unsigned long long base = a.base ? *a.base : 0ull;
   const unsigned long long avail = a.base ? (a.limit > base ? a.limit - base : 0ull) : a.avail;
   const uint8_t* in = a.in + base;
-  int bad = 0;
-  unsigned long long first = 0, words = 0;
-  int minexp = 0;
-  if (lane == 0) {
-    if (a.payload > avail || get_u32(in) != ZC_MAGIC || get_u32(in + 4) != ZC_VERSION ||
-        (int)get_u32(in + 8) != a.nx || (int)get_u32(in + 12) != a.ny ||
-        (int)get_u32(in + 16) != a.nz || get_u64(in + 24) != (unsigned long long)a.nblocks ||
-        get_u32(in + 32) != (uint32_t)ZC_CHUNK || get_u32(in + 36) != (uint32_t)a.nchunks ||
-        get_u32(in + 56) != (uint32_t)(ZC_S | (ZC_G << 8))) {
-      bad = 1;
-    } else {
-      minexp = (int)get_u32(in + 20);
-      const unsigned long long total = get_u64(in + 40);
-      first = get_u64(in + a.chunk_table + 8ull * chunk);
-      const unsigned long long next =
-          chunk + 1 < a.nchunks ? get_u64(in + a.chunk_table + 8ull * (chunk + 1)) : total;
-      if (total > (avail - a.payload) / 8 || first > next || next > total ||
-          next - first > (unsigned long long)kWordsMax)
-        bad = 1;
-      words = next - first;
-    }
-  }
-  bad = __shfl_sync(0xffffffffu, bad, 0);
-  if (bad) {
+  if (a.payload > avail) {  // the tables do not fit (warp-uniform)
     if (lane == 0) atomicOr(a.status, ST_CORRUPT);
     return;
   }
-  first = __shfl_sync(0xffffffffu, first, 0);
-  words = __shfl_sync(0xffffffffu, words, 0);
-  minexp = __shfl_sync(0xffffffffu, minexp, 0);
+  // One round trip: lanes 0-7 load the eight header words, lanes 8-9 this
+  // chunk's and the next chunk's payload offsets (all inside the tables).
+  unsigned long long hw = 0;
+  if (lane < 8)
+    hw = get_u64(in + 8 * lane);
+  else if (lane == 8 || (lane == 9 && chunk + 1 < a.nchunks))
+    hw = get_u64(in + a.chunk_table + 8ull * (chunk + lane - 8));
+  const unsigned long long h0 = __shfl_sync(0xffffffffu, hw, 0), h1 = __shfl_sync(0xffffffffu, hw, 1);
+  const unsigned long long h2 = __shfl_sync(0xffffffffu, hw, 2), h3 = __shfl_sync(0xffffffffu, hw, 3);
+  const unsigned long long h4 = __shfl_sync(0xffffffffu, hw, 4), h5 = __shfl_sync(0xffffffffu, hw, 5);
+  const unsigned long long h7 = __shfl_sync(0xffffffffu, hw, 7);
+  const unsigned long long first = __shfl_sync(0xffffffffu, hw, 8);
+  unsigned long long next = __shfl_sync(0xffffffffu, hw, 9);
+  const unsigned long long pay_words = h5;  // payload words (bytes 40..47)
+  if (chunk + 1 >= a.nchunks) next = pay_words;
+  const bool bad = (uint32_t)h0 != ZC_MAGIC || (uint32_t)(h0 >> 32) != ZC_VERSION ||
+                   (int)(uint32_t)h1 != a.nx || (int)(uint32_t)(h1 >> 32) != a.ny ||
+                   (int)(uint32_t)h2 != a.nz || h3 != (unsigned long long)a.nblocks ||
+                   (uint32_t)h4 != (uint32_t)ZC_CHUNK || (uint32_t)(h4 >> 32) != (uint32_t)a.nchunks ||
+                   (uint32_t)h7 != (uint32_t)(ZC_S | (ZC_G << 8)) || pay_words > (avail - a.payload) / 8 ||
+                   first > next || next > pay_words || next - first > (unsigned long long)kWordsMax;
+  if (bad) {  // warp-uniform
+    if (lane == 0) atomicOr(a.status, ST_CORRUPT);
+    return;
+  }
+  const int minexp = (int)(uint32_t)(h2 >> 32);  // bytes 20..23
+  const unsigned long long words = next - first;
   const long blk = chunk * ZC_CHUNK + lane;
   const bool valid = blk < a.nblocks;
   const int len = valid ? (int)*reinterpret_cast<const uint16_t*>(in + a.length_table + 2ull * blk) : 0;
@@ -768,6 +774,8 @@ static EncArgs encode_args(const float* in, Grid g, int minexp, uint8_t* out,
   a.status = d_status;
   a.desc = nullptr;
   a.ticket = nullptr;
+  a.live = nullptr;
+  a.live_ntx = 0;
   return a;
 }
 
@@ -780,9 +788,17 @@ size_t zfp_encode_scratch_bytes(int nx, int ny, int nz) {
 cudaError_t zfp_encode_launch(const float* in, Grid g, int minexp, uint8_t* out,
                               const unsigned long long* d_base, size_t capacity,
                               unsigned long long* d_size, int* d_status, void* scratch,
-                              cudaStream_t s) {
+                              cudaStream_t s, const LiveMap* live) {
   if (!scratch) return cudaErrorInvalidValue;
   EncArgs a = encode_args(in, g, minexp, out, d_base, capacity, d_size, d_status);
+  if (live && live->words) {
+    // the map must have been written at exactly this tolerance's threshold
+    if (live->threshold != live_threshold(minexp) || !(live->threshold > 0.0f) ||
+        live->ntx != (g.pitch + 63) / 64 || live->nby != (int)a.nby)
+      return cudaErrorInvalidValue;
+    a.live = live->words;
+    a.live_ntx = live->ntx;
+  }
   const long ntiles = (a.nchunks + kTile - 1) / kTile;
   StageArgs st;
   st.stage = static_cast<unsigned long long*>(scratch);

@@ -63,6 +63,23 @@ struct ZLayout {
 };
 ZLayout zlayout(int nx, int ny, int nz);
 
+// Per 4x4x4 block of a field, whether any value reaches `threshold` (or is
+// NaN/Inf): bit bx % 16 of words[(bz * nby + by) * ntx + bx / 16], ntx =
+// ceil(pitch / 64) (one 16-bit word per 64-cell tile row segment).  Written
+// by a forward step for the field it produces; with threshold =
+// 2^(minexp - 11) a block without its bit codes as zero (no coded plane), so
+// the encoder need not read it.
+struct LiveMap {
+  uint16_t* words;
+  float threshold;
+  int ntx, nby;
+};
+size_t live_map_words(Grid g);
+// The threshold for tolerance exponent minexp, or 0 when no map can stand in
+// for the encoder's own test at that tolerance (below 2^-126 a block of
+// subnormals can still code planes).
+float live_threshold(int minexp);
+
 // Compress one pitched field into out (device), which has `capacity` bytes
 // counted from the device offset *d_base (bytes; NULL = 0).  The stream size
 // is written to *d_size (device); flags go to *d_status.  Two passes with no
@@ -70,10 +87,12 @@ ZLayout zlayout(int nx, int ny, int nz);
 // one CTA per tile of chunks places the words.  `scratch` must hold
 // zfp_encode_scratch_bytes() bytes.  Asynchronous.
 size_t zfp_encode_scratch_bytes(int nx, int ny, int nz);
+// With live (nullable, written for this field at this tolerance's
+// threshold), blocks without their live bit are coded as zero unread.
 cudaError_t zfp_encode_launch(const float* in, Grid g, int minexp, uint8_t* out,
                               const unsigned long long* d_base, size_t capacity,
                               unsigned long long* d_size, int* d_status, void* scratch,
-                              cudaStream_t s);
+                              cudaStream_t s, const LiveMap* live = nullptr);
 // Single-pass variant whose scratch is only nchunks+1 words (per-chunk
 // look-back descriptors and a ticket), zeroed here: chunks find their offset
 // by a decoupled look-back over their predecessors.  Same stream.
@@ -139,9 +158,10 @@ struct StencilParams {
 
 // out = step(cur, prev) with one point injection (cell index in the pitched
 // layout, or -1) of value q * b / (1 + s dt/2).  out may alias prev.
+// With live (nullable), also writes the liveness map of out (every word).
 cudaError_t stencil_step_launch(const StencilParams& p, const float* cur, const float* prev,
                                 float* out, long src_cell, const float* d_wavelet, int n,
-                                cudaStream_t s);
+                                cudaStream_t s, const LiveMap* live = nullptr);
 // Adjoint step with fused imaging:
 //   out = step(cur, prev);  grad -= weight * uk * (out - 2 cur + prev) / dt^2
 // (receiver injection is added afterwards by inject_adjoint_launch).

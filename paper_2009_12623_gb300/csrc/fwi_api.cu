@@ -608,11 +608,11 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
   s = cs.main;  // the sweep's own stream from here on
   const cudaStream_t enc_s = cs.s;
   const cudaStream_t dec_s = kDecodeOverlap ? cs.s : s;
-  auto store_field = [&](const float* f, int j) -> int {
+  auto store_field = [&](const float* f, int j, const LiveMap* live = nullptr) -> int {
     if (lossy) {
       CK(slot_offset_launch(offs, sizes, j, enc_s));
       CK(zfp_encode_launch(f, G, minexp, store->arena, offs + j, store->capacity, sizes + j,
-                           sw.d_status, scratch, enc_s));
+                           sw.d_status, scratch, enc_s, live));
       CK(track_peak_launch(offs, sizes, j, d_peak, enc_s));
     } else {
       CK(cudaMemcpyAsync(store->arena + (size_t)j * raw_slot, f, fbytes, cudaMemcpyDeviceToDevice, enc_s));
@@ -632,6 +632,24 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
   cudaEvent_t f_read[2] = {cs.ev[0], cs.ev[1]};
   bool f_pending[2] = {false, false};
   auto fidx = [&](const float* p) { return p == fbuf[0] ? 0 : 1; };
+  // Full-history compressed sweeps: each forward step also records which
+  // blocks of the state it writes reach the tolerance's last coded plane
+  // (one liveness map per state buffer, reused with it), and the encoder
+  // codes the other blocks as zero without reading them.  Every stored state
+  // of these schedules comes from a forward step of the same sweep.
+  const bool live_maps = lossy && do_fwd && (pol->mode == FWI_CKPT_FULL || pol->mode == FWI_CKPT_SUBSAMPLE) &&
+                         live_threshold(minexp) > 0.0f;
+  LiveMap lmap[2] = {};
+  if (live_maps) {
+    for (int i = 0; i < 2; ++i) {
+      lmap[i].words = pool.get<uint16_t>(live_map_words(G));
+      lmap[i].threshold = live_threshold(minexp);
+      lmap[i].ntx = (G.pitch + 63) / 64;
+      lmap[i].nby = (G.ny + 3) / 4;
+    }
+    if (pool.failed) return FWI_ERR_NOMEM;
+  }
+  auto live_of = [&](const float* f) -> const LiveMap* { return live_maps ? &lmap[fidx(f)] : nullptr; };
   // full-history decode double buffer
   float* dbuf[2] = {rprev, ring[0]};
   cudaEvent_t d_ready[2] = {cs.ev[2], cs.ev[3]}, d_used[2] = {cs.ev[4], cs.ev[5]};
@@ -693,10 +711,10 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
           break;
         }
         if (state_step != a.step) return FWI_ERR_ARG;
-        const int w = fidx(fprev);  // the step overwrites fprev
+        const int w = fidx(fprev);  // the step overwrites fprev (and its liveness map)
         if (f_pending[w]) CK(cudaStreamWaitEvent(s, f_read[w], 0));
         f_pending[w] = false;
-        CK(stencil_step_launch(sw.sp, fcur, fprev, fprev, sw.src, sw.d_wavelet, a.step, s));
+        CK(stencil_step_launch(sw.sp, fcur, fprev, fprev, sw.src, sw.d_wavelet, a.step, s, live_of(fprev)));
         std::swap(fprev, fcur);
         state_step = a.step + 1;
         if (a.kind == FWI_ACT_ADVANCE)
@@ -710,7 +728,7 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
           CK(cudaStreamWaitEvent(enc_s, ev_adv, 0));
           const int j1 = binom ? bslot((int)bstack.size(), 1) : slot[{a.step, 1}];
           const int j0 = binom ? bslot((int)bstack.size(), 0) : (a.arg == 2 ? slot[{a.step, 0}] : -1);
-          if ((st = store_field(fcur, j1))) return st;
+          if ((st = store_field(fcur, j1, live_of(fcur)))) return st;
           if (a.arg == 2 && (st = store_field(fprev, j0))) return st;
           CK(cudaEventRecord(f_read[fidx(fcur)], enc_s));
           f_pending[fidx(fcur)] = true;

@@ -388,16 +388,22 @@ def test_slot_bytes_report_each_checkpoint(cuda, two_layer):
         assert b10.size == st.stats()["n_checkpoints"] and b10.size % 2 == 0 and b10.size <= 2 * (g.nt // 10 + 1)
 
 
-@pytest.mark.parametrize("which,atol", [("two_layer", 1e-4), ("two_layer", 1e-2), ("ragged", 1e-5)])
+@pytest.mark.parametrize("which,atol", [("two_layer", 1e-4), ("two_layer", 1e-2), ("ragged", 1e-5),
+                                        ("mid", 1e-4)])
 def test_zero_block_skipping_is_exact(cuda, two_layer, which, atol):
-    """The full-history reverse sweep leaves the blocks a compressed state codes
-    as zero undecoded and skips u^k and g there (the imaging term is exactly 0).
-    Every-1 checkpoint pairs decode the very same streams in full, so the two
-    gradients must agree bit for bit; the early, sparse states of these shots
-    are mostly zero blocks."""
+    """Blocks a state codes as zero are skipped on both sides of the full-history
+    sweep: the forward step marks the blocks that reach the tolerance's last
+    coded plane and the encoder codes the others as zero unread; the reverse
+    sweep leaves them undecoded and skips u^k and g there (the imaging term is
+    exactly 0).  Every-1 checkpoint pairs read and decode every block, so the
+    two gradients must agree bit for bit.  The early states of these shots are
+    mostly zero blocks; the mid-size grid (ragged in every direction) runs the
+    forward step in several z-chunks per tile column."""
     from paper_2009_12623_gb300 import synth
-    shot, d_obs = two_layer if which == "two_layer" else (_small_shot(), None)
-    if d_obs is None:
+    if which == "two_layer":
+        shot, d_obs = two_layer
+    else:
+        shot = _small_shot() if which == "ragged" else _small_shot(nx=161, ny=122, nz=150, nt=70, nbl=8)
         d_obs = np.zeros((shot.geom.nt, len(shot.rec)))
     g_full, phi_full, _ = _grad(cuda, shot, d_obs, 1, atol=atol)
     g_k1, phi_k1, _ = _grad(cuda, shot, d_obs, 2, k=1, atol=atol)
