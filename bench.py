@@ -188,24 +188,32 @@ def config_dict(args, shot, policy):
 
 
 # kernel classes of the gradient that run alone on the sweep's stream
-IN_ORDER = ("stencil_forward", "stencil_adjoint_imaging", "zfp_decode")
+IN_ORDER = ("stencil_forward", "stencil_adjoint", "zfp_decode")
 
 
-def kernel_bytes(cells, enc_bytes_per_launch, live=1.0):
+def kernel_bytes(cells, enc_bytes_per_launch, live=1.0, image_in_decoder=False):
     """Algorithmic bytes per launch (halos and scratch excluded).  `live` is
     the mean fraction of each stored state's blocks that are not coded as
-    zero: the full-history reverse sweep neither writes (decoder) nor reads
-    u^k and g (adjoint) in the others."""
+    zero.  Full-history compressed sweeps (image_in_decoder) run the adjoint
+    step as a plain step (16 B/cell) and image in the decoder, which reads
+    the stream and, for live blocks only, lambda_{k-1}, lambda_k,
+    lambda_{k+1} and g and writes g (20 B/value); otherwise the adjoint
+    stencil images (16 + 12 B/cell: u^k and g) after a decoder that writes
+    u^k (4 B/value)."""
+    if image_in_decoder:
+        adj, dec = 16.0 * cells, 20.0 * live * cells + enc_bytes_per_launch
+    else:
+        adj, dec = (16.0 + 12.0 * live) * cells, 4.0 * live * cells + enc_bytes_per_launch
     return {
         "stencil_forward": 16.0 * cells,                 # read u^n, u^{n-1}, m; write u^{n+1}
-        "stencil_adjoint_imaging": (16.0 + 12.0 * live) * cells,  # + read u^k, read/write g where live
+        "stencil_adjoint": adj,
         "zfp_encode": 4.0 * cells + enc_bytes_per_launch,
-        "zfp_decode": 4.0 * live * cells + enc_bytes_per_launch,
+        "zfp_decode": dec,
     }
 
 
 def source_hash(kernel: str) -> str:
-    files = {"stencil_forward": "stencil.cu", "stencil_adjoint_imaging": "stencil.cu",
+    files = {"stencil_forward": "stencil.cu", "stencil_adjoint": "stencil.cu",
              "zfp_encode": "codec.cu", "zfp_decode": "codec.cu"}
     csrc = os.path.join(ROOT, "paper_2009_12623_gb300", "csrc")
     h = hashlib.sha256()
@@ -429,8 +437,9 @@ def run_fwi(args):
     enc_bytes = stats["used_bytes"] / max(1, stats["n_checkpoints"])
     nblocks = -(-g.nx // 4) * -(-g.ny // 4) * -(-g.nz // 4)
     zero_blocks = store.slot_zero_blocks().astype(np.float64)
-    live = float(1.0 - zero_blocks.mean() / nblocks) if policy_mode == api.FWI_CKPT_FULL and args.atol > 0 else 1.0
-    kb = kernel_bytes(cells, enc_bytes, live)
+    full_lossy = policy_mode == api.FWI_CKPT_FULL and args.atol > 0
+    live = float(1.0 - zero_blocks.mean() / nblocks) if full_lossy else 1.0
+    kb = kernel_bytes(cells, enc_bytes, live, image_in_decoder=full_lossy)
     timed = {k: v for k, v in prof.items() if k in kb and v[1] > 0}
     # The dominant kernel is the one with the most device time among those that run alone, in
     # order, on the sweep's stream.  The encoder runs on a second stream beside the next forward

@@ -369,7 +369,7 @@ uint64_t fwi_kernel_launch_count(void);
 
 /* Per-kernel timing for roofline accounting.  While enabled, the library
  * records a CUDA event pair on the launching stream around every launch of
- * the timed classes (0 forward stencil, 1 adjoint stencil with imaging,
+ * the timed classes (0 forward stencil, 1 adjoint stencil (imaging fused or not),
  * 2 codec encode, 3 codec decode, 4 everything else); read returns, per
  * class, the summed device milliseconds and launch count since the last
  * reset (it waits for recorded events).  n must be >= 5. */

@@ -30,7 +30,7 @@ EXPORTS = [
     "fwi_batch_forward", "fwi_batch_adjoint", "fwi_batch_get_stats", "fwi_selftest_bounded_wait",
     "fwi_selftest_damped_quotient",
 ]
-KERNEL_CLASSES = ["stencil_forward", "stencil_adjoint_imaging", "zfp_encode", "zfp_decode", "other"]
+KERNEL_CLASSES = ["stencil_forward", "stencil_adjoint", "zfp_encode", "zfp_decode", "other"]
 
 
 class FwiError(RuntimeError):

@@ -556,7 +556,94 @@ struct SmemSink {  // plane b of one lane's block
   }
 };
 
-__global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(DecArgs a) {
+// Decode-and-image tail of the decoder (one lane per block).  Every lane of
+// the warp reaches the warp barrier; then each lane's decoded block moves to
+// the warp's shared memory (the plane masks and staged words are dead by
+// then), freeing its 64 registers so that the loads of lambda_{k-1},
+// lambda_k, lambda_{k+1} and g for several rows can be in flight at once.
+constexpr int kVStride = 68;  // floats per lane: 16-byte rows, conflict-free per quarter warp
+static_assert(32 * kVStride * 4 <= 2 * 32 * 32 * 4 + (kAsmWords + 2) * 8, "decoded blocks fit the warp's area");
+
+__device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& im, long blk, bool valid, int minexp,
+                                             uint32_t* lo, uint32_t* hi, const unsigned long long* words_src,
+                                             long start, int len, long nwords, float* warp_area) {
+  const int lane = threadIdx.x & 31;
+  bool work = valid;
+  int emax = 0, planes = 0;
+  if (work) {
+    SReader rd{words_src, start, start + len, nwords};
+    SmemSink sink{lo + lane, hi + lane};
+    if (!decode_planes_mem(rd, minexp, sink, emax, planes) || rd.pos != rd.end) {
+      atomicOr(a.status, ST_CORRUPT);
+      work = false;
+    } else if (planes == 0) {
+      work = false;  // a zero block images nothing
+    }
+  }
+  float v[64];
+  if (work) {
+    uint32_t u[64];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+      const bool coded = b >= 32 - planes;
+      u[b] = coded ? lo[b * 32 + lane] : 0u;
+      u[32 + b] = coded ? hi[b * 32 + lane] : 0u;
+    }
+    dequantise(u, emax, planes, v);
+  }
+  __syncwarp();  // every lane is done with the warp's plane masks and words
+  float* vs = warp_area + lane * kVStride;
+  if (work) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      *reinterpret_cast<float4*>(vs + 4 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  }
+  asm volatile("" ::: "memory");  // the rows below read the block back from shared memory
+  if (!work) return;
+  long bx, by, bz;
+  block_xyz(blk, a.nbx, a.nby, a.nblocks, bx, by, bz);
+  const long xb = 4 * bx;
+  const bool vec = a.vec_ok && xb + 3 < a.nx;
+  const bool store = im.rec_block[blk] != 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const long z = 4 * bz + k;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long y = 4 * by + j;
+      if (z < a.nz && y < a.ny) {
+        const long c = a.pitch * (y + (long)a.ny * z) + xb;
+        const float4 u4 = *reinterpret_cast<const float4*>(vs + 4 * j + 16 * k);
+        const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
+        if (vec) {
+          const float4 lp = __ldg(reinterpret_cast<const float4*>(im.lp + c));
+          const float4 lc = __ldg(reinterpret_cast<const float4*>(im.lc + c));
+          const float4 ln = __ldg(reinterpret_cast<const float4*>(im.ln + c));
+          float4 g = *reinterpret_cast<const float4*>(im.g + c);
+          g.x = image_update(g.x, uv[0], lp.x, lc.x, ln.x, im.idt2);
+          g.y = image_update(g.y, uv[1], lp.y, lc.y, ln.y, im.idt2);
+          g.z = image_update(g.z, uv[2], lp.z, lc.z, ln.z, im.idt2);
+          g.w = image_update(g.w, uv[3], lp.w, lc.w, ln.w, im.idt2);
+          *reinterpret_cast<float4*>(im.g + c) = g;
+          if (store) *reinterpret_cast<float4*>(a.out + c) = u4;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (xb + i < a.nx) {
+              im.g[c + i] = image_update(im.g[c + i], uv[i], __ldg(im.lp + c + i), __ldg(im.lc + c + i),
+                                         __ldg(im.ln + c + i), im.idt2);
+              if (store) a.out[c + i] = uv[i];
+            }
+        }
+      }
+    }
+  }
+}
+
+// IMAGE: instead of writing the decoded block, image it (ImageArgs) and
+// write it only where im.rec_block flags it; blocks coded as zero are skipped.
+template <bool IMAGE>
+__global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(DecArgs a, ImageArgs im) {
   extern __shared__ unsigned long long dec_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned char* wbase = reinterpret_cast<unsigned char*>(dec_smem) + (size_t)wid * kDecSmemPerWarp;
@@ -618,6 +705,11 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(
   __syncwarp();
   if ((unsigned long long)total > 64ull * words) {
     if (lane == 0) atomicOr(a.status, ST_CORRUPT);
+    return;
+  }
+  if constexpr (IMAGE) {
+    image_blocks(a, im, blk, valid, minexp, lo, hi, staged ? sbuf : src, (long)(incl - (unsigned)len), len,
+                 (long)words, reinterpret_cast<float*>(wbase));
     return;
   }
   if (!valid) return;
@@ -742,7 +834,9 @@ static cudaError_t ensure_codec_attributes() {
   if (g_attr_done[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(k_encode_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmem);
+  e = cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmem);
   if (e != cudaSuccess) return e;
   g_attr_done[dev] = true;
   return cudaSuccess;
@@ -853,8 +947,8 @@ ZeroBlocks zero_blocks(const uint8_t* arena, const unsigned long long* base, siz
   return z;
 }
 
-cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_base, size_t avail,
-                              float* out, Grid g, int* d_status, cudaStream_t s, bool skip_zero) {
+static DecArgs decode_args(const uint8_t* in, const unsigned long long* d_base, size_t avail, float* out, Grid g,
+                           int* d_status, bool skip_zero) {
   ZLayout L = zlayout(g.nx, g.ny, g.nz);
   DecArgs a;
   a.in = in;
@@ -876,10 +970,31 @@ cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_bas
   a.payload = L.payload;
   a.status = d_status;
   a.skip_zero = skip_zero;
+  return a;
+}
+
+cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_base, size_t avail,
+                              float* out, Grid g, int* d_status, cudaStream_t s, bool skip_zero) {
+  const DecArgs a = decode_args(in, d_base, avail, out, g, d_status, skip_zero);
   const cudaError_t e = ensure_codec_attributes();
   if (e != cudaSuccess) return e;
   const int ps = prof_begin(KC_ZFP_DECODE, s);
-  k_decode<<<(unsigned)((L.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, kDecSmem, s>>>(a);
+  k_decode<false><<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, kDecSmem, s>>>(a, ImageArgs{});
+  prof_end(ps, s);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t zfp_decode_image_launch(const uint8_t* in, const unsigned long long* d_base, size_t avail,
+                                    float* uk_out, Grid g, int* d_status, const ImageArgs& im, cudaStream_t s) {
+  if (!im.lp || !im.lc || !im.ln || !im.g || !im.rec_block) return cudaErrorInvalidValue;
+  const DecArgs a = decode_args(in, d_base, avail, uk_out, g, d_status, true);
+  if (a.vec_ok && ((((uintptr_t)im.lp | (uintptr_t)im.lc | (uintptr_t)im.ln | (uintptr_t)im.g) & 15) != 0))
+    return cudaErrorInvalidValue;
+  const cudaError_t e = ensure_codec_attributes();
+  if (e != cudaSuccess) return e;
+  const int ps = prof_begin(KC_ZFP_DECODE, s);
+  k_decode<true><<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, kDecSmem, s>>>(a, im);
   prof_end(ps, s);
   count_launch();
   return cudaGetLastError();

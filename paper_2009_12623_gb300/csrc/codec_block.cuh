@@ -410,42 +410,75 @@ FZ_HD bool decode_planes(R& rd, int minexp, uint32_t* u, int& emax, int& planes)
 }
 
 // decode_planes with a rolled plane loop: plane b goes to sink(b, mask) for
-// every coded plane (uncoded planes are left to the caller).
+// every coded plane (uncoded planes are left to the caller).  The next bits
+// are held in a 64-bit window w (wa of them valid, the rest zero), refilled
+// from the reader only when a field runs past it, so most verbatim runs,
+// group bits and runs are taken from registers.
 template <class R, class K>
 FZ_HD bool decode_planes_mem(R& rd, int minexp, K& sink, int& emax, int& planes) {
   emax = 0;
   planes = 0;
   if (rd.pos + 1 > rd.end) return false;
-  const uint64_t hdr = rd.peek();
-  if (!(hdr & 1ull)) {
+  uint64_t w = rd.peek();
+  int wa = 64;
+  if (!(w & 1ull)) {
     rd.pos += 1;
     return true;
   }
   if (rd.pos + 9 > rd.end) return false;
-  emax = (int)((hdr >> 1) & 0xffull) - 127;
+  emax = (int)((w >> 1) & 0xffull) - 127;
   rd.pos += 9;
+  w >>= 9;
+  wa -= 9;
   planes = planes_for(emax, minexp);
   if (planes == 0) return false;
   int n = 0;
   for (int b = 31; b >= 32 - planes; --b) {
     uint64_t m = 0ull;
-    if (n > 0) {
+    if (n > 0) {  // the bits of the coefficients already significant, verbatim
       if (rd.pos + n > rd.end) return false;
-      const uint64_t v = rd.peek();
-      m = n < 64 ? (v & ((1ull << n) - 1ull)) : v;
+      if (wa < n) {
+        w = rd.peek();
+        wa = 64;
+      }
       rd.pos += n;
+      if (n < 64) {
+        m = w & ((1ull << n) - 1ull);
+        w >>= n;
+        wa -= n;
+      } else {
+        m = w;
+        w = 0ull;
+        wa = 0;
+      }
     }
     while (n < 64) {
       if (rd.pos + 1 > rd.end) return false;
-      const uint64_t t = rd.peek();
+      if (wa < 1) {
+        w = rd.peek();
+        wa = 64;
+      }
+      const bool group = (w & 1ull) != 0ull;
       rd.pos += 1;
-      if (!(t & 1ull)) break;
-      // the 63 bits after the group bit usually hold the run's 1; else peek again
-      uint64_t pk = t >> 1;
-      if (!pk) pk = rd.peek();
-      const int j = pk ? ctz64(pk) : 64;
+      w >>= 1;
+      wa -= 1;
+      if (!group) break;
+      // the run: j zero bits, then the newly significant coefficient's 1
+      int j = w ? ctz64(w) : 64;
+      if (j >= wa) {
+        w = rd.peek();
+        wa = 64;
+        j = w ? ctz64(w) : 64;
+      }
       if (j >= 64 - n || rd.pos + j + 1 > rd.end) return false;
       rd.pos += j + 1;
+      if (j < 63) {
+        w >>= j + 1;
+        wa -= j + 1;
+      } else {
+        w = 0ull;
+        wa = 0;
+      }
       m |= 1ull << (n + j);
       n += j + 1;
     }

@@ -142,7 +142,36 @@ __device__ __forceinline__ const uint16_t* zero_table(const ZeroBlocks& z) {
 __device__ __forceinline__ bool block_live(const uint16_t* tab, const ZeroBlocks& z, int x, int y, int zz) {
   return !tab || tab[((long)(zz >> 2) * z.nby + (y >> 2)) * z.nbx + (x >> 2)] != 1;
 }
+// One cell of the imaging sum (Eq. 4): g - u (l_prev - 2 l_cur + l_next) idt2
+// with l_prev = lambda_{k-1}, l_cur = lambda_k, l_next = lambda_{k+1} and
+// idt2 = weight / dt^2, in one fixed rounding sequence (no contraction), so
+// that every kernel that images a cell produces the same bits.
+__device__ __forceinline__ float image_update(float g, float u, float lp, float lc, float ln, float idt2) {
+  const float d = __fadd_rn(__fsub_rn(lp, __fmul_rn(2.0f, lc)), ln);
+  return __fsub_rn(g, __fmul_rn(__fmul_rn(u, d), idt2));
+}
 #endif
+
+// Imaging from a compressed state (full-history reverse sweep): the decoder
+// of u^k, run after the adjoint step that produced lambda_{k-1}, images the
+// blocks u^k does not code as zero straight from its registers,
+//   g -= u^k (lp - 2 lc + ln) idt2,
+// and writes decoded values only for blocks flagged in rec_block (those with
+// receivers, whose imaging correction the receiver injection adds).
+struct ImageArgs {
+  const float* lp;   // lambda_{k-1}
+  const float* lc;   // lambda_k
+  const float* ln;   // lambda_{k+1}
+  float* g;
+  float idt2;
+  const uint8_t* rec_block;  // per block (codec block order): 1 = holds a receiver
+};
+cudaError_t zfp_decode_image_launch(const uint8_t* in, const unsigned long long* d_base, size_t avail,
+                                    float* uk_out, Grid g, int* d_status, const ImageArgs& im,
+                                    cudaStream_t s);
+// rec_block[b] = 1 for every 4x4x4 block b (codec order) holding a receiver cell
+// (pitched cell indices), 0 elsewhere.
+cudaError_t receiver_blocks_launch(const long* rec_cell, int nrec, Grid g, uint8_t* rec_block, cudaStream_t s);
 
 // ---- stencil ----------------------------------------------------------------
 struct StencilParams {
@@ -156,6 +185,10 @@ struct StencilParams {
   int* status;     // device status word (bounded waits report timeouts here)
 };
 
+// The adjoint recurrence's step without imaging (the same step, no source),
+// timed as an adjoint-stencil launch; out may alias prev.
+cudaError_t stencil_adjoint_step_launch(const StencilParams& p, const float* cur, const float* prev,
+                                        float* out, cudaStream_t s);
 // out = step(cur, prev) with one point injection (cell index in the pitched
 // layout, or -1) of value q * b / (1 + s dt/2).  out may alias prev.
 // With live (nullable), also writes the liveness map of out (every word).

@@ -661,6 +661,21 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
   // injection read the stream's length table and skip those blocks, where
   // the imaging term is exactly zero.
   const bool skip_zero = full && lossy;
+  // ... and their imaging moves into the decoder: the adjoint step becomes a
+  // plain step into a third lambda buffer (lambda_{k+1} stays readable), then
+  // the decoder of u^k images its non-zero blocks from registers.
+  const bool image_in_decoder = skip_zero && do_rev;
+  float* lthird = nullptr;
+  uint8_t* rec_block = nullptr;
+  if (image_in_decoder) {
+    const ZLayout ZL = zlayout(G.nx, G.ny, G.nz);
+    lthird = pool.get<float>(G.cells());
+    rec_block = pool.get<uint8_t>((size_t)ZL.nblocks);
+    if (pool.failed) return FWI_ERR_NOMEM;
+    CK(cudaMemsetAsync(lthird, 0, fbytes, s));
+    CK(receiver_blocks_launch(sw.rec_cell, nrec, G, rec_block, s));
+  }
+  const float idt2 = 1.0f / (sw.sp.dt * sw.sp.dt);  // as the adjoint stencil forms it
   int next_buf = 0;
   auto issue_decode = [&](int k) -> int {  // u^k into the next decode buffer, on dec_s
     const int b = next_buf;
@@ -745,6 +760,7 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
         bstack.pop_back();
         break;
       case FWI_ACT_RESTORE:
+        if (a.arg == 1 && image_in_decoder) break;  // decoded (and imaged) by its adjoint step
         if (a.arg == 1) {  // single state u^k (decoded ahead on the codec stream)
           if (!(d_issued[0] && d_step[0] == a.step) && !(d_issued[1] && d_step[1] == a.step)) {
             if ((st = issue_decode(a.step))) return st;
@@ -790,6 +806,27 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
           CK(inject_adjoint_launch(sw.sp, sw.rec_cell, sw.rec_fac, nrec, resid + (size_t)(k - 1) * nrec,
                                    lnext, nullptr, gacc, 0.f, s));
           std::swap(lcur, lnext);
+          break;
+        }
+        if (image_in_decoder) {
+          const int j = slot[{k, 1}];
+          const ZeroBlocks zb = zero_blocks(store->arena, offs + j, store->capacity, G);
+          CK(stencil_adjoint_step_launch(sw.sp, lcur, lnext, lthird, s));  // lambda_{k-1}
+          ImageArgs im;
+          im.lp = lthird;
+          im.lc = lcur;
+          im.ln = lnext;
+          im.g = gacc;
+          im.idt2 = idt2 * (float)weight;
+          im.rec_block = rec_block;
+          CK(zfp_decode_image_launch(store->arena, offs + j, store->capacity, dbuf[0], G, sw.d_status, im, s));
+          CK(inject_adjoint_launch(sw.sp, sw.rec_cell, sw.rec_fac, nrec, resid + (size_t)(k - 1) * nrec,
+                                   lthird, dbuf[0], gacc, (float)weight, s, &zb));
+          float* t = lnext;  // lambda_{k+1} <- lambda_k <- lambda_{k-1}
+          lnext = lcur;
+          lcur = lthird;
+          lthird = t;
+          avail[k] = nullptr;
           break;
         }
         const float* uk = avail[k];
