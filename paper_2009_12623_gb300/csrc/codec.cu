@@ -544,7 +544,11 @@ __device__ __forceinline__ unsigned long long get_u64(const uint8_t* p) {
 
 // Shared memory of the decoder, per warp: the plane masks of each lane's
 // block ([plane][lane] low / high halves) and the chunk's words when they fit.
-constexpr int kDecSmemPerWarp = 2 * 32 * 32 * 4 + (kAsmWords + 2) * 8;
+// The decoder stages up to kDecWords words of a chunk (larger chunks are read
+// from global memory by the bounded reader): 10 KB per warp, so five CTAs of
+// the imaging decoder (96 registers) fit an SM.
+constexpr int kDecWords = 256;
+constexpr int kDecSmemPerWarp = 2 * 32 * 32 * 4 + (kDecWords + 2) * 8;
 constexpr int kDecSmem = kWarps * kDecSmemPerWarp;
 
 struct SmemSink {  // plane b of one lane's block
@@ -562,7 +566,7 @@ struct SmemSink {  // plane b of one lane's block
 // then), freeing its 64 registers so that the loads of lambda_{k-1},
 // lambda_k, lambda_{k+1} and g for several rows can be in flight at once.
 constexpr int kVStride = 68;  // floats per lane: 16-byte rows, conflict-free per quarter warp
-static_assert(32 * kVStride * 4 <= 2 * 32 * 32 * 4 + (kAsmWords + 2) * 8, "decoded blocks fit the warp's area");
+static_assert(32 * kVStride * 4 <= kDecSmemPerWarp, "decoded blocks fit the warp's area");
 
 __device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& im, long blk, bool valid, int minexp,
                                              uint32_t* lo, uint32_t* hi, const unsigned long long* words_src,
@@ -643,7 +647,8 @@ __device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& 
 // IMAGE: instead of writing the decoded block, image it (ImageArgs) and
 // write it only where im.rec_block flags it; blocks coded as zero are skipped.
 template <bool IMAGE>
-__global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(DecArgs a, ImageArgs im) {
+__global__ void __launch_bounds__(ZC_CHUNK * kWarps, IMAGE ? FWI_DEC_MIN_CTAS + 1 : FWI_DEC_MIN_CTAS)
+    k_decode(DecArgs a, ImageArgs im) {
   extern __shared__ unsigned long long dec_smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned char* wbase = reinterpret_cast<unsigned char*>(dec_smem) + (size_t)wid * kDecSmemPerWarp;
@@ -691,7 +696,7 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(
   const int len = valid ? (int)*reinterpret_cast<const uint16_t*>(in + a.length_table + 2ull * blk) : 0;
   // stage the chunk's words (when they fit) and scan the block lengths
   const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in + a.payload) + first;
-  const bool staged = words <= (unsigned long long)kAsmWords;  // warp-uniform
+  const bool staged = words <= (unsigned long long)kDecWords;  // warp-uniform
   if (staged) {
     for (unsigned long long w = lane; w < words; w += 32) sbuf[w] = __ldg(src + w);
   }
