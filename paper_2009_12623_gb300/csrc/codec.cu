@@ -41,7 +41,7 @@ using namespace zblock;
 constexpr int kWordsMax = (ZC_CHUNK * ZC_MAXBITS + 63) / 64;  // 1061 words
 constexpr int kWarps = 4;                                       // chunks per CTA
 #ifndef FWI_ENC_MIN_CTAS
-#define FWI_ENC_MIN_CTAS 4  // resident CTAs per SM the staged encoder is compiled for
+#define FWI_ENC_MIN_CTAS 5  // resident CTAs per SM the staged encoder is compiled for
 #endif
 #ifndef FWI_DEC_MIN_CTAS
 #define FWI_DEC_MIN_CTAS 4  // the same for the decoder
@@ -317,7 +317,7 @@ __device__ __forceinline__ void gather_block(const EncArgs& a, long bx, long by,
 // conflict-free), and a buffer in which the chunk's words are assembled when
 // they fit (always for real wavefields; a larger chunk is assembled directly
 // in its global staging slot instead).
-constexpr int kAsmWords = 512;
+constexpr int kAsmWords = 256;  // 10 KB of shared memory per warp: five encoder CTAs fit an SM
 constexpr int kEncSmemPerWarp = 2 * 32 * 32 * 4 + (kAsmWords + 1) * 8;
 constexpr int kEncSmem = kWarps * kEncSmemPerWarp;
 
@@ -544,12 +544,13 @@ __device__ __forceinline__ unsigned long long get_u64(const uint8_t* p) {
 
 // Shared memory of the decoder, per warp: the plane masks of each lane's
 // block ([plane][lane] low / high halves) and the chunk's words when they fit.
-// The decoder stages up to kDecWords words of a chunk (larger chunks are read
-// from global memory by the bounded reader): 10 KB per warp, so five CTAs of
-// the imaging decoder (96 registers) fit an SM.
-constexpr int kDecWords = 256;
-constexpr int kDecSmemPerWarp = 2 * 32 * 32 * 4 + (kDecWords + 2) * 8;
-constexpr int kDecSmem = kWarps * kDecSmemPerWarp;
+// The decoder stages up to dec_words(IMAGE) words of a chunk (larger chunks
+// are read from global memory by the bounded reader).  The imaging decoder
+// (96 registers) keeps 10 KB per warp so that five of its CTAs fit an SM; the
+// plain decoder (128 registers, four CTAs) stages up to 512 words.
+constexpr int dec_words(bool image) { return image ? 256 : 512; }
+constexpr int dec_smem_per_warp(bool image) { return 2 * 32 * 32 * 4 + (dec_words(image) + 2) * 8; }
+constexpr int dec_smem(bool image) { return kWarps * dec_smem_per_warp(image); }
 
 struct SmemSink {  // plane b of one lane's block
   uint32_t* lo;
@@ -566,7 +567,7 @@ struct SmemSink {  // plane b of one lane's block
 // then), freeing its 64 registers so that the loads of lambda_{k-1},
 // lambda_k, lambda_{k+1} and g for several rows can be in flight at once.
 constexpr int kVStride = 68;  // floats per lane: 16-byte rows, conflict-free per quarter warp
-static_assert(32 * kVStride * 4 <= kDecSmemPerWarp, "decoded blocks fit the warp's area");
+static_assert(32 * kVStride * 4 <= dec_smem_per_warp(true), "decoded blocks fit the warp's area");
 
 __device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& im, long blk, bool valid, int minexp,
                                              uint32_t* lo, uint32_t* hi, const unsigned long long* words_src,
@@ -649,9 +650,9 @@ __device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& 
 template <bool IMAGE>
 __global__ void __launch_bounds__(ZC_CHUNK * kWarps, IMAGE ? FWI_DEC_MIN_CTAS + 1 : FWI_DEC_MIN_CTAS)
     k_decode(DecArgs a, ImageArgs im) {
-  extern __shared__ unsigned long long dec_smem[];
+  extern __shared__ unsigned long long dec_smem_buf[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned char* wbase = reinterpret_cast<unsigned char*>(dec_smem) + (size_t)wid * kDecSmemPerWarp;
+  unsigned char* wbase = reinterpret_cast<unsigned char*>(dec_smem_buf) + (size_t)wid * dec_smem_per_warp(IMAGE);
   uint32_t* lo = reinterpret_cast<uint32_t*>(wbase);  // [32][32]
   uint32_t* hi = lo + 32 * 32;
   unsigned long long* sbuf = reinterpret_cast<unsigned long long*>(hi + 32 * 32);
@@ -696,7 +697,7 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, IMAGE ? FWI_DEC_MIN_CTAS + 
   const int len = valid ? (int)*reinterpret_cast<const uint16_t*>(in + a.length_table + 2ull * blk) : 0;
   // stage the chunk's words (when they fit) and scan the block lengths
   const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in + a.payload) + first;
-  const bool staged = words <= (unsigned long long)kDecWords;  // warp-uniform
+  const bool staged = words <= (unsigned long long)dec_words(IMAGE);  // warp-uniform
   if (staged) {
     for (unsigned long long w = lane; w < words; w += 32) sbuf[w] = __ldg(src + w);
   }
@@ -839,9 +840,9 @@ static cudaError_t ensure_codec_attributes() {
   if (g_attr_done[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(k_encode_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmem);
+  e = cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dec_smem(false));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmem);
+  e = cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dec_smem(true));
   if (e != cudaSuccess) return e;
   g_attr_done[dev] = true;
   return cudaSuccess;
@@ -984,7 +985,8 @@ cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_bas
   const cudaError_t e = ensure_codec_attributes();
   if (e != cudaSuccess) return e;
   const int ps = prof_begin(KC_ZFP_DECODE, s);
-  k_decode<false><<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, kDecSmem, s>>>(a, ImageArgs{});
+  k_decode<false><<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, dec_smem(false), s>>>(
+      a, ImageArgs{});
   prof_end(ps, s);
   count_launch();
   return cudaGetLastError();
@@ -999,7 +1001,7 @@ cudaError_t zfp_decode_image_launch(const uint8_t* in, const unsigned long long*
   const cudaError_t e = ensure_codec_attributes();
   if (e != cudaSuccess) return e;
   const int ps = prof_begin(KC_ZFP_DECODE, s);
-  k_decode<true><<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, kDecSmem, s>>>(a, im);
+  k_decode<true><<<(unsigned)((a.nchunks + kWarps - 1) / kWarps), ZC_CHUNK * kWarps, dec_smem(true), s>>>(a, im);
   prof_end(ps, s);
   count_launch();
   return cudaGetLastError();
