@@ -41,10 +41,10 @@ using namespace zblock;
 constexpr int kWordsMax = (ZC_CHUNK * ZC_MAXBITS + 63) / 64;  // 1061 words
 constexpr int kWarps = 4;                                       // chunks per CTA
 #ifndef FWI_ENC_MIN_CTAS
-#define FWI_ENC_MIN_CTAS 5  // resident CTAs per SM the staged encoder is compiled for
+#define FWI_ENC_MIN_CTAS 6  // resident CTAs per SM the staged encoder is compiled for
 #endif
 #ifndef FWI_DEC_MIN_CTAS
-#define FWI_DEC_MIN_CTAS 4  // the same for the decoder
+#define FWI_DEC_MIN_CTAS 6  // the same for the decoder
 #endif
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
@@ -317,7 +317,7 @@ __device__ __forceinline__ void gather_block(const EncArgs& a, long bx, long by,
 // conflict-free), and a buffer in which the chunk's words are assembled when
 // they fit (always for real wavefields; a larger chunk is assembled directly
 // in its global staging slot instead).
-constexpr int kAsmWords = 256;  // 10 KB of shared memory per warp: five encoder CTAs fit an SM
+constexpr int kAsmWords = 128;  // 9 KB of shared memory per warp: six encoder CTAs fit an SM
 constexpr int kEncSmemPerWarp = 2 * 32 * 32 * 4 + (kAsmWords + 1) * 8;
 constexpr int kEncSmem = kWarps * kEncSmemPerWarp;
 
@@ -544,11 +544,10 @@ __device__ __forceinline__ unsigned long long get_u64(const uint8_t* p) {
 
 // Shared memory of the decoder, per warp: the plane masks of each lane's
 // block ([plane][lane] low / high halves) and the chunk's words when they fit.
-// The decoder stages up to dec_words(IMAGE) words of a chunk (larger chunks
-// are read from global memory by the bounded reader).  The imaging decoder
-// (96 registers) keeps 10 KB per warp so that five of its CTAs fit an SM; the
-// plain decoder (128 registers, four CTAs) stages up to 512 words.
-constexpr int dec_words(bool image) { return image ? 256 : 512; }
+// The decoder stages up to dec_words() words of a chunk (larger chunks are
+// read from global memory by the bounded reader): 9 KB of shared memory per
+// warp, so that six decoder CTAs fit an SM.
+constexpr int dec_words(bool) { return 128; }
 constexpr int dec_smem_per_warp(bool image) { return 2 * 32 * 32 * 4 + (dec_words(image) + 2) * 8; }
 constexpr int dec_smem(bool image) { return kWarps * dec_smem_per_warp(image); }
 
@@ -561,17 +560,22 @@ struct SmemSink {  // plane b of one lane's block
   }
 };
 
-// Decode-and-image tail of the decoder (one lane per block).  Every lane of
-// the warp reaches the warp barrier; then each lane's decoded block moves to
-// the warp's shared memory (the plane masks and staged words are dead by
-// then), freeing its 64 registers so that the loads of lambda_{k-1},
-// lambda_k, lambda_{k+1} and g for several rows can be in flight at once.
+// Tail of the decoder (one lane per block).  Every lane of the warp reaches
+// the warp barrier; then each lane's decoded block moves to the warp's shared
+// memory (the plane masks and staged words are dead by then), freeing its 64
+// registers, so the decoder fits six CTAs per SM and several rows' loads and
+// stores can be in flight at once.  IMAGE: image the block (ImageArgs) and
+// write it only where im.rec_block flags it; else write it.  Blocks coded as
+// zero are skipped when imaging or with a.skip_zero.
 constexpr int kVStride = 68;  // floats per lane: 16-byte rows, conflict-free per quarter warp
-static_assert(32 * kVStride * 4 <= dec_smem_per_warp(true), "decoded blocks fit the warp's area");
+static_assert(32 * kVStride * 4 <= dec_smem_per_warp(true) && 32 * kVStride * 4 <= dec_smem_per_warp(false),
+              "decoded blocks fit the warp's area");
 
-__device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& im, long blk, bool valid, int minexp,
-                                             uint32_t* lo, uint32_t* hi, const unsigned long long* words_src,
-                                             long start, int len, long nwords, float* warp_area) {
+template <bool IMAGE>
+__device__ __forceinline__ void finish_blocks(const DecArgs& a, const ImageArgs& im, long blk, bool valid,
+                                              int minexp, uint32_t* lo, uint32_t* hi,
+                                              const unsigned long long* words_src, long start, int len,
+                                              long nwords, float* warp_area) {
   const int lane = threadIdx.x & 31;
   bool work = valid;
   int emax = 0, planes = 0;
@@ -581,27 +585,31 @@ __device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& 
     if (!decode_planes_mem(rd, minexp, sink, emax, planes) || rd.pos != rd.end) {
       atomicOr(a.status, ST_CORRUPT);
       work = false;
-    } else if (planes == 0) {
-      work = false;  // a zero block images nothing
+    } else if (planes == 0 && (IMAGE || a.skip_zero)) {
+      work = false;  // a zero block: its consumers skip it
     }
   }
+  const bool coded = work && planes > 0;  // otherwise a zero block to be written (plain decoder)
   float v[64];
-  if (work) {
+  if (coded) {
     uint32_t u[64];
 #pragma unroll
     for (int b = 0; b < 32; ++b) {
-      const bool coded = b >= 32 - planes;
-      u[b] = coded ? lo[b * 32 + lane] : 0u;
-      u[32 + b] = coded ? hi[b * 32 + lane] : 0u;
+      const bool in = b >= 32 - planes;
+      u[b] = in ? lo[b * 32 + lane] : 0u;
+      u[32 + b] = in ? hi[b * 32 + lane] : 0u;
     }
     dequantise(u, emax, planes, v);
   }
   __syncwarp();  // every lane is done with the warp's plane masks and words
   float* vs = warp_area + lane * kVStride;
-  if (work) {
+  if (coded) {
 #pragma unroll
     for (int i = 0; i < 16; ++i)
       *reinterpret_cast<float4*>(vs + 4 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else if (work) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) *reinterpret_cast<float4*>(vs + 4 * i) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   asm volatile("" ::: "memory");  // the rows below read the block back from shared memory
   if (!work) return;
@@ -609,7 +617,7 @@ __device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& 
   block_xyz(blk, a.nbx, a.nby, a.nblocks, bx, by, bz);
   const long xb = 4 * bx;
   const bool vec = a.vec_ok && xb + 3 < a.nx;
-  const bool store = im.rec_block[blk] != 0;
+  const bool store = !IMAGE || im.rec_block[blk] != 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const long z = 4 * bz + k;
@@ -621,22 +629,25 @@ __device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& 
         const float4 u4 = *reinterpret_cast<const float4*>(vs + 4 * j + 16 * k);
         const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
         if (vec) {
-          const float4 lp = __ldg(reinterpret_cast<const float4*>(im.lp + c));
-          const float4 lc = __ldg(reinterpret_cast<const float4*>(im.lc + c));
-          const float4 ln = __ldg(reinterpret_cast<const float4*>(im.ln + c));
-          float4 g = *reinterpret_cast<const float4*>(im.g + c);
-          g.x = image_update(g.x, uv[0], lp.x, lc.x, ln.x, im.idt2);
-          g.y = image_update(g.y, uv[1], lp.y, lc.y, ln.y, im.idt2);
-          g.z = image_update(g.z, uv[2], lp.z, lc.z, ln.z, im.idt2);
-          g.w = image_update(g.w, uv[3], lp.w, lc.w, ln.w, im.idt2);
-          *reinterpret_cast<float4*>(im.g + c) = g;
+          if (IMAGE) {
+            const float4 lp = __ldg(reinterpret_cast<const float4*>(im.lp + c));
+            const float4 lc = __ldg(reinterpret_cast<const float4*>(im.lc + c));
+            const float4 ln = __ldg(reinterpret_cast<const float4*>(im.ln + c));
+            float4 g = *reinterpret_cast<const float4*>(im.g + c);
+            g.x = image_update(g.x, uv[0], lp.x, lc.x, ln.x, im.idt2);
+            g.y = image_update(g.y, uv[1], lp.y, lc.y, ln.y, im.idt2);
+            g.z = image_update(g.z, uv[2], lp.z, lc.z, ln.z, im.idt2);
+            g.w = image_update(g.w, uv[3], lp.w, lc.w, ln.w, im.idt2);
+            *reinterpret_cast<float4*>(im.g + c) = g;
+          }
           if (store) *reinterpret_cast<float4*>(a.out + c) = u4;
         } else {
 #pragma unroll
           for (int i = 0; i < 4; ++i)
             if (xb + i < a.nx) {
-              im.g[c + i] = image_update(im.g[c + i], uv[i], __ldg(im.lp + c + i), __ldg(im.lc + c + i),
-                                         __ldg(im.ln + c + i), im.idt2);
+              if (IMAGE)
+                im.g[c + i] = image_update(im.g[c + i], uv[i], __ldg(im.lp + c + i), __ldg(im.lc + c + i),
+                                           __ldg(im.ln + c + i), im.idt2);
               if (store) a.out[c + i] = uv[i];
             }
         }
@@ -645,11 +656,9 @@ __device__ __forceinline__ void image_blocks(const DecArgs& a, const ImageArgs& 
   }
 }
 
-// IMAGE: instead of writing the decoded block, image it (ImageArgs) and
-// write it only where im.rec_block flags it; blocks coded as zero are skipped.
+// IMAGE: instead of writing the decoded block, image it (finish_blocks).
 template <bool IMAGE>
-__global__ void __launch_bounds__(ZC_CHUNK * kWarps, IMAGE ? FWI_DEC_MIN_CTAS + 1 : FWI_DEC_MIN_CTAS)
-    k_decode(DecArgs a, ImageArgs im) {
+__global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(DecArgs a, ImageArgs im) {
   extern __shared__ unsigned long long dec_smem_buf[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned char* wbase = reinterpret_cast<unsigned char*>(dec_smem_buf) + (size_t)wid * dec_smem_per_warp(IMAGE);
@@ -713,55 +722,8 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, IMAGE ? FWI_DEC_MIN_CTAS + 
     if (lane == 0) atomicOr(a.status, ST_CORRUPT);
     return;
   }
-  if constexpr (IMAGE) {
-    image_blocks(a, im, blk, valid, minexp, lo, hi, staged ? sbuf : src, (long)(incl - (unsigned)len), len,
-                 (long)words, reinterpret_cast<float*>(wbase));
-    return;
-  }
-  if (!valid) return;
-  const long start = (long)(incl - (unsigned)len);
-  SReader rd{staged ? sbuf : src, start, start + len, (long)words};
-  int emax = 0, planes = 0;
-  SmemSink sink{lo + lane, hi + lane};
-  if (!decode_planes_mem(rd, minexp, sink, emax, planes) || rd.pos != rd.end) {
-    atomicOr(a.status, ST_CORRUPT);
-    return;
-  }
-  if (a.skip_zero && planes == 0) return;  // a zero block: its consumers skip it
-  float v[64];
-  {
-    uint32_t u[64];
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      const bool coded = b >= 32 - planes;
-      u[b] = coded ? lo[b * 32 + lane] : 0u;
-      u[32 + b] = coded ? hi[b * 32 + lane] : 0u;
-    }
-    dequantise(u, emax, planes, v);
-  }
-  long bx, by, bz;
-  block_xyz(blk, a.nbx, a.nby, a.nblocks, bx, by, bz);
-  const long xb = 4 * bx;
-  const bool vec = a.vec_ok && xb + 3 < a.nx;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const long z = 4 * bz + k;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const long y = 4 * by + j;
-      if (z < a.nz && y < a.ny) {
-        float* row = a.out + a.pitch * (y + (long)a.ny * z);
-        const int o = 4 * j + 16 * k;
-        if (vec) {
-          *reinterpret_cast<float4*>(row + xb) = make_float4(v[o], v[o + 1], v[o + 2], v[o + 3]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (xb + i < a.nx) row[xb + i] = v[o + i];
-        }
-      }
-    }
-  }
+  finish_blocks<IMAGE>(a, im, blk, valid, minexp, lo, hi, staged ? sbuf : src, (long)(incl - (unsigned)len), len,
+                       (long)words, reinterpret_cast<float*>(wbase));
 }
 
 // Blocks coded as zero (length one bit) per slot: grid (ctas per slot, slots).
