@@ -437,3 +437,26 @@ def test_slot_zero_blocks_match_the_oracle_streams(cuda, oracle, two_layer):
         assert z[0] > z[-1] > 0
         api.gradient(g, m, shot.wavelet, shot.src, rec, obs, st, mode=api.FWI_CKPT_FULL, atol=0.0)
         assert np.all(st.slot_zero_blocks() == 0)
+
+
+@pytest.mark.parametrize("atol", [1e-4, 1e-2])
+def test_nonfinite_wavefield_is_reported_not_skipped(cuda, atol):
+    """The forward step's block-liveness map counts NaN and Inf as live, so a
+    non-finite state still reaches the encoder and the full-history
+    compressed gradient fails with FWI_ERR_NONFINITE instead of coding the
+    block as zero; the caller's gradient is left untouched.  The model is
+    finite and positive (setup accepts it) but one cell's tiny squared
+    slowness makes the leapfrog step there unstable: the wavefield
+    overflows to Inf and NaN within a few steps of the wave's arrival."""
+    from paper_2009_12623_gb300 import _lib, api, synth
+    shot = _small_shot(nt=30)
+    m = synth.slowness2(shot.v0).copy()
+    m[12, 14, 10] = 1e-30
+    d_obs = torch.zeros((shot.geom.nt, len(shot.rec)), device=cuda)
+    grad = torch.full(shot.geom.shape, 7.0, device=cuda)
+    with api.CheckpointStore(1 << 28) as st:
+        with pytest.raises(api.FwiError) as e:
+            api.gradient(shot.geom, _dev(cuda, m), shot.wavelet, shot.src, _dev(cuda, shot.rec), d_obs, st,
+                         mode=api.FWI_CKPT_FULL, atol=atol, grad=grad)
+    assert e.value.status == _lib.FWI_ERR_NONFINITE
+    assert bool((grad == 7.0).all())
