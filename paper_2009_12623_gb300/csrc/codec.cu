@@ -516,7 +516,6 @@ struct DecArgs {
   long nbx, nby, nblocks, nchunks;
   unsigned long long chunk_table, length_table, payload;
   int* status;
-  bool skip_zero;  // leave blocks coded as zero unwritten
 };
 
 // Bit reader over a chunk's words (staged in shared memory, or in global
@@ -565,8 +564,8 @@ struct SmemSink {  // plane b of one lane's block
 // memory (the plane masks and staged words are dead by then), freeing its 64
 // registers, so the decoder fits six CTAs per SM and several rows' loads and
 // stores can be in flight at once.  IMAGE: image the block (ImageArgs) and
-// write it only where im.rec_block flags it; else write it.  Blocks coded as
-// zero are skipped when imaging or with a.skip_zero.
+// write it only where im.rec_block flags it, skipping blocks coded as zero;
+// else write it.
 constexpr int kVStride = 68;  // floats per lane: 16-byte rows, conflict-free per quarter warp
 static_assert(32 * kVStride * 4 <= dec_smem_per_warp(true) && 32 * kVStride * 4 <= dec_smem_per_warp(false),
               "decoded blocks fit the warp's area");
@@ -585,8 +584,8 @@ __device__ __forceinline__ void finish_blocks(const DecArgs& a, const ImageArgs&
     if (!decode_planes_mem(rd, minexp, sink, emax, planes) || rd.pos != rd.end) {
       atomicOr(a.status, ST_CORRUPT);
       work = false;
-    } else if (planes == 0 && (IMAGE || a.skip_zero)) {
-      work = false;  // a zero block: its consumers skip it
+    } else if (planes == 0 && IMAGE) {
+      work = false;  // a zero block images nothing
     }
   }
   const bool coded = work && planes > 0;  // otherwise a zero block to be written (plain decoder)
@@ -675,12 +674,16 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(
     return;
   }
   // One round trip: lanes 0-7 load the eight header words, lanes 8-9 this
-  // chunk's and the next chunk's payload offsets (all inside the tables).
+  // chunk's and the next chunk's payload offsets, every lane its block's
+  // coded length (all inside the tables).
+  const long blk = chunk * ZC_CHUNK + lane;
+  const bool valid = blk < a.nblocks;
   unsigned long long hw = 0;
   if (lane < 8)
     hw = get_u64(in + 8 * lane);
   else if (lane == 8 || (lane == 9 && chunk + 1 < a.nchunks))
     hw = get_u64(in + a.chunk_table + 8ull * (chunk + lane - 8));
+  const int len = valid ? (int)*reinterpret_cast<const uint16_t*>(in + a.length_table + 2ull * blk) : 0;
   const unsigned long long h0 = __shfl_sync(0xffffffffu, hw, 0), h1 = __shfl_sync(0xffffffffu, hw, 1);
   const unsigned long long h2 = __shfl_sync(0xffffffffu, hw, 2), h3 = __shfl_sync(0xffffffffu, hw, 3);
   const unsigned long long h4 = __shfl_sync(0xffffffffu, hw, 4), h5 = __shfl_sync(0xffffffffu, hw, 5);
@@ -701,11 +704,15 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_DEC_MIN_CTAS) k_decode(
   }
   const int minexp = (int)(uint32_t)(h2 >> 32);  // bytes 20..23
   const unsigned long long words = next - first;
-  const long blk = chunk * ZC_CHUNK + lane;
-  const bool valid = blk < a.nblocks;
-  const int len = valid ? (int)*reinterpret_cast<const uint16_t*>(in + a.length_table + 2ull * blk) : 0;
-  // stage the chunk's words (when they fit) and scan the block lengths
   const unsigned long long* src = reinterpret_cast<const unsigned long long*>(in + a.payload) + first;
+  // A chunk of blocks that are all the single bit 0 (one payload word, zero)
+  // has nothing to image.
+  if (IMAGE && words == 1 && __all_sync(0xffffffffu, !valid || len == 1)) {
+    unsigned long long w0 = 0;
+    if (lane == 0) w0 = __ldg(src);
+    if (__shfl_sync(0xffffffffu, w0, 0) == 0ull) return;  // else the blocks below report the corruption
+  }
+  // stage the chunk's words (when they fit) and scan the block lengths
   const bool staged = words <= (unsigned long long)dec_words(IMAGE);  // warp-uniform
   if (staged) {
     for (unsigned long long w = lane; w < words; w += 32) sbuf[w] = __ldg(src + w);
@@ -916,7 +923,7 @@ ZeroBlocks zero_blocks(const uint8_t* arena, const unsigned long long* base, siz
 }
 
 static DecArgs decode_args(const uint8_t* in, const unsigned long long* d_base, size_t avail, float* out, Grid g,
-                           int* d_status, bool skip_zero) {
+                           int* d_status) {
   ZLayout L = zlayout(g.nx, g.ny, g.nz);
   DecArgs a;
   a.in = in;
@@ -937,13 +944,12 @@ static DecArgs decode_args(const uint8_t* in, const unsigned long long* d_base, 
   a.length_table = L.length_table;
   a.payload = L.payload;
   a.status = d_status;
-  a.skip_zero = skip_zero;
   return a;
 }
 
 cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_base, size_t avail,
-                              float* out, Grid g, int* d_status, cudaStream_t s, bool skip_zero) {
-  const DecArgs a = decode_args(in, d_base, avail, out, g, d_status, skip_zero);
+                              float* out, Grid g, int* d_status, cudaStream_t s) {
+  const DecArgs a = decode_args(in, d_base, avail, out, g, d_status);
   const cudaError_t e = ensure_codec_attributes();
   if (e != cudaSuccess) return e;
   const int ps = prof_begin(KC_ZFP_DECODE, s);
@@ -957,7 +963,7 @@ cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_bas
 cudaError_t zfp_decode_image_launch(const uint8_t* in, const unsigned long long* d_base, size_t avail,
                                     float* uk_out, Grid g, int* d_status, const ImageArgs& im, cudaStream_t s) {
   if (!im.lp || !im.lc || !im.ln || !im.g || !im.rec_block) return cudaErrorInvalidValue;
-  const DecArgs a = decode_args(in, d_base, avail, uk_out, g, d_status, true);
+  const DecArgs a = decode_args(in, d_base, avail, uk_out, g, d_status);
   if (a.vec_ok && ((((uintptr_t)im.lp | (uintptr_t)im.lc | (uintptr_t)im.ln | (uintptr_t)im.g) & 15) != 0))
     return cudaErrorInvalidValue;
   const cudaError_t e = ensure_codec_attributes();

@@ -104,17 +104,15 @@ cudaError_t zfp_encode_chained_launch(const float* in, Grid g, int minexp, uint8
 
 // Decompress a stream located at in + *d_base (d_base NULL = 0) of at most
 // `avail` bytes into a pitched field.  Asynchronous; errors go to *d_status.
-// With skip_zero, blocks the stream codes as zero (the single bit 0) are not
-// written: the caller's consumers must then skip them (see ZeroBlocks).
 cudaError_t zfp_decode_launch(const uint8_t* in, const unsigned long long* d_base,
                               size_t avail, float* out, Grid g, int* d_status,
-                              cudaStream_t s, bool skip_zero = false);
+                              cudaStream_t s);
 
 // Where a compressed field's block-length table lies, for kernels that
-// consume the field decoded with skip_zero: a block whose coded length is one
-// bit decodes to exactly 0, so its cells are neither read nor needed.  The
-// stream starts at arena + *base (a device word); arena == NULL means "no
-// table: every block is live".
+// consume its decoded values only where the imaging decoder wrote them: a
+// block whose coded length is one bit decodes to exactly 0, so its cells are
+// neither written nor needed.  The stream starts at arena + *base (a device
+// word); arena == NULL means "no table: every block is live".
 struct ZeroBlocks {
   const uint8_t* arena;
   const unsigned long long* base;
@@ -198,11 +196,9 @@ cudaError_t stencil_step_launch(const StencilParams& p, const float* cur, const 
 // Adjoint step with fused imaging:
 //   out = step(cur, prev);  grad -= weight * uk * (out - 2 cur + prev) / dt^2
 // (receiver injection is added afterwards by inject_adjoint_launch).
-// With zb (nullable), blocks of uk that zb marks as zero are not read and
-// their grad cells are left as they are (the imaging term there is exactly 0).
 cudaError_t stencil_adjoint_launch(const StencilParams& p, const float* cur, const float* prev,
                                    float* out, const float* uk, float* grad, float weight,
-                                   cudaStream_t s, const ZeroBlocks* zb = nullptr);
+                                   cudaStream_t s);
 // out[rec] += r * fac; if uk: grad[rec] -= weight * uk[rec] * r * fac / dt^2
 // (skipped where zb, nullable, marks the block of uk as zero).
 cudaError_t inject_adjoint_launch(const StencilParams& p, const long* rec_cell, const float* rec_fac,

@@ -619,9 +619,9 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
     }
     return FWI_OK;
   };
-  auto load_field = [&](int j, float* f, cudaStream_t st, bool skip_zero = false) -> int {
+  auto load_field = [&](int j, float* f, cudaStream_t st) -> int {
     if (lossy) {
-      CK(zfp_decode_launch(store->arena, offs + j, store->capacity, f, G, sw.d_status, st, skip_zero));
+      CK(zfp_decode_launch(store->arena, offs + j, store->capacity, f, G, sw.d_status, st));
     } else {
       CK(cudaMemcpyAsync(f, store->arena + (size_t)j * raw_slot, fbytes, cudaMemcpyDeviceToDevice, st));
     }
@@ -654,17 +654,14 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
   float* dbuf[2] = {rprev, ring[0]};
   cudaEvent_t d_ready[2] = {cs.ev[2], cs.ev[3]}, d_used[2] = {cs.ev[4], cs.ev[5]};
   bool d_issued[2] = {false, false}, d_inuse[2] = {false, false};
-  int d_step[2] = {-1, -1}, d_slot[2] = {-1, -1};
+  int d_step[2] = {-1, -1};
   const bool full = pol->mode == FWI_CKPT_FULL || pol->mode == FWI_CKPT_SUBSAMPLE;
-  // Full-history compressed states are decoded without their zero blocks
-  // (one-bit blocks decode to exactly 0); the adjoint step and the receiver
-  // injection read the stream's length table and skip those blocks, where
-  // the imaging term is exactly zero.
-  const bool skip_zero = full && lossy;
-  // ... and their imaging moves into the decoder: the adjoint step becomes a
-  // plain step into a third lambda buffer (lambda_{k+1} stays readable), then
-  // the decoder of u^k images its non-zero blocks from registers.
-  const bool image_in_decoder = skip_zero && do_rev;
+  // Full-history compressed reverse sweeps image in the decoder: the adjoint
+  // step becomes a plain step into a third lambda buffer (lambda_{k+1} stays
+  // readable), then the decoder of u^k images its blocks that are not coded
+  // as zero (one-bit blocks decode to exactly 0, so their imaging term is
+  // exactly zero); the receiver injection skips those blocks too.
+  const bool image_in_decoder = full && lossy && do_rev;
   float* lthird = nullptr;
   uint8_t* rec_block = nullptr;
   if (image_in_decoder) {
@@ -684,11 +681,10 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
     // far (the state may have been stored moments ago)
     if (!kDecodeOverlap) CK(cs.join());
     if (d_inuse[b]) CK(cudaStreamWaitEvent(dec_s, d_used[b], 0));
-    if ((st = load_field(slot[{k, 1}], dbuf[b], dec_s, skip_zero))) return st;
+    if ((st = load_field(slot[{k, 1}], dbuf[b], dec_s))) return st;
     CK(cudaEventRecord(d_ready[b], dec_s));
     d_issued[b] = true;
     d_step[b] = k;
-    d_slot[b] = slot[{k, 1}];
     return FWI_OK;
   };
   cudaEvent_t ev_adv = cs.ev[6];
@@ -846,11 +842,9 @@ int run_sweeps(const fwi_geometry* g, const float* d_m, const float* h_wavelet, 
           uk = state_step == k ? fcur : nullptr;
         }
         if (!uk) return FWI_ERR_ARG;
-        ZeroBlocks zb{};
-        if (full && skip_zero) zb = zero_blocks(store->arena, offs + d_slot[b], store->capacity, G);
-        CK(stencil_adjoint_launch(sw.sp, lcur, lnext, lnext, uk, gacc, (float)weight, s, &zb));
+        CK(stencil_adjoint_launch(sw.sp, lcur, lnext, lnext, uk, gacc, (float)weight, s));
         CK(inject_adjoint_launch(sw.sp, sw.rec_cell, sw.rec_fac, nrec, resid + (size_t)(k - 1) * nrec,
-                                 lnext, uk, gacc, (float)weight, s, &zb));
+                                 lnext, uk, gacc, (float)weight, s));
         if (full) {
           CK(cudaEventRecord(d_used[b], s));
           d_inuse[b] = true;
