@@ -460,3 +460,22 @@ def test_nonfinite_wavefield_is_reported_not_skipped(cuda, atol):
                          mode=api.FWI_CKPT_FULL, atol=atol, grad=grad)
     assert e.value.status == _lib.FWI_ERR_NONFINITE
     assert bool((grad == 7.0).all())
+
+
+def test_subsampling_compressed_tracks_oracle(cuda, oracle):
+    """Subsampled imaging (Sec. 4.7) with compressed states: every f-th state
+    stored at atol, the reverse sweep alternating plain adjoint steps with
+    imaging ones (decoded and imaged by the decoder).  The GPU's compression
+    error against its own raw subsampled gradient matches the oracle's."""
+    from paper_2009_12623_gb300 import synth
+    shot = _small_shot()
+    og = _og(oracle, shot.geom)
+    m = synth.slowness2(shot.v0).astype(np.float64)
+    w = shot.wavelet.astype(np.float64)
+    d_obs = oracle.forward(og, synth.slowness2(shot.v_true).astype(np.float64), w, shot.src, shot.rec)
+    g_oraw, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs, mode=4, k=3)
+    g_oz, *_ = oracle.gradient(og, m, w, shot.src, shot.rec, d_obs, mode=4, k=3, atol=1e-4)
+    g_graw, *_ = _grad(cuda, shot, d_obs, 4, k=3)
+    g_gz, _, stats = _grad(cuda, shot, d_obs, 4, k=3, atol=1e-4)
+    _same_compression_error(g_gz, g_graw, g_oz, g_oraw)
+    assert stats["n_checkpoints"] == shot.geom.nt // 3
