@@ -520,14 +520,16 @@ struct DecArgs {
 
 // Bit reader over a chunk's words (staged in shared memory, or in global
 // memory for a chunk larger than the staging buffer); words at index >= nw
-// read as zero, so a peek at the end never leaves the chunk.
+// read as zero, so a peek at the end never leaves the chunk.  Positions are
+// bits from the chunk's first word (at most 64 kWordsMax, checked by the
+// caller), so 32-bit arithmetic holds them.
 struct SReader {
   const unsigned long long* buf;
-  long pos;
-  long end;
-  long nw;
+  int pos;
+  int end;
+  int nw;
   __device__ __forceinline__ unsigned long long peek() const {
-    const long w = pos >> 6;
+    const int w = pos >> 6;
     const int o = (int)(pos & 63);
     unsigned long long v = w < nw ? buf[w] : 0ull;
     v >>= o;
@@ -579,7 +581,7 @@ __device__ __forceinline__ void finish_blocks(const DecArgs& a, const ImageArgs&
   bool work = valid;
   int emax = 0, planes = 0;
   if (work) {
-    SReader rd{words_src, start, start + len, nwords};
+    SReader rd{words_src, (int)start, (int)(start + len), (int)nwords};
     SmemSink sink{lo + lane, hi + lane};
     if (!decode_planes_mem(rd, minexp, sink, emax, planes) || rd.pos != rd.end) {
       atomicOr(a.status, ST_CORRUPT);

@@ -350,70 +350,17 @@ FZ_HD void emit_mem(W& w, const P& pl, int emax, int planes) {
   }
 }
 
-// Inverse of emit.  R provides pos/end (bit positions) and peek() (the next
-// 64 bits).  Returns false on a malformed block.
-template <class R>
-FZ_HD bool decode_planes(R& rd, int minexp, uint32_t* u, int& emax, int& planes) {
-#pragma unroll
-  for (int i = 0; i < 64; ++i) u[i] = 0u;
-  emax = 0;
-  planes = 0;
-  if (rd.pos + 1 > rd.end) return false;
-  const uint64_t hdr = rd.peek();
-  if (!(hdr & 1ull)) {
-    rd.pos += 1;
-    return true;
-  }
-  if (rd.pos + 9 > rd.end) return false;
-  emax = (int)((hdr >> 1) & 0xffull) - 127;
-  rd.pos += 9;
-  planes = planes_for(emax, minexp);
-  if (planes == 0) return false;
-  int n = 0;
-  bool ok = true;
-#pragma unroll
-  for (int b = 31; b >= 0; --b) {
-    if (b >= 32 - planes && ok) {
-      uint64_t m = 0ull;
-      if (n > 0) {
-        if (rd.pos + n > rd.end) {
-          ok = false;
-        } else {
-          const uint64_t v = rd.peek();
-          m = n < 64 ? (v & ((1ull << n) - 1ull)) : v;
-          rd.pos += n;
-        }
-      }
-      while (n < 64 && ok) {
-        if (rd.pos + 1 > rd.end) {
-          ok = false;
-          break;
-        }
-        const uint64_t t = rd.peek();
-        rd.pos += 1;
-        if (!(t & 1ull)) break;
-        const uint64_t pk = rd.peek();
-        const int j = pk ? ctz64(pk) : 64;
-        if (j >= 64 - n || rd.pos + j + 1 > rd.end) {
-          ok = false;
-          break;
-        }
-        rd.pos += j + 1;
-        m |= 1ull << (n + j);
-        n += j + 1;
-      }
-      u[b] = (uint32_t)m;
-      u[32 + b] = (uint32_t)(m >> 32);
-    }
-  }
-  return ok;
-}
-
-// decode_planes with a rolled plane loop: plane b goes to sink(b, mask) for
-// every coded plane (uncoded planes are left to the caller).  The next bits
-// are held in a 64-bit window w (wa of them valid, the rest zero), refilled
-// from the reader only when a field runs past it, so most verbatim runs,
-// group bits and runs are taken from registers.
+// Inverse of emit: plane b goes to sink(b, mask) for every coded plane
+// (uncoded planes are left to the caller).  R provides pos/end (bit
+// positions) and peek() (the next 64 bits, zero past the words it holds).
+// The next bits are held in a 64-bit window w (wa of them valid), refilled
+// from the reader only when a field runs past it.  One loop pass reads one
+// group test and its run, or finishes a plane and takes the next plane's
+// verbatim bits, so a lane's passes follow its own block's runs rather than
+// the warp's largest run count in every plane.  Whatever the bits, the loop
+// stops after at most 64 runs and one pass per plane; the bounds are checked
+// once, by the caller, which rejects the block unless exactly end - pos bits
+// were consumed.  Returns false on a malformed header or run.
 template <class R, class K>
 FZ_HD bool decode_planes_mem(R& rd, int minexp, K& sink, int& emax, int& planes) {
   emax = 0;
@@ -432,11 +379,44 @@ FZ_HD bool decode_planes_mem(R& rd, int minexp, K& sink, int& emax, int& planes)
   wa -= 9;
   planes = planes_for(emax, minexp);
   if (planes == 0) return false;
-  int n = 0;
-  for (int b = 31; b >= 32 - planes; --b) {
-    uint64_t m = 0ull;
+  const int blast = 32 - planes;
+  int b = 31, n = 0;  // the top plane has no verbatim bits
+  uint64_t m = 0ull;
+  for (;;) {
+    if (n < 64) {  // a group test
+      if (wa < 1) {
+        w = rd.peek();
+        wa = 64;
+      }
+      const bool group = (w & 1ull) != 0ull;
+      rd.pos += 1;
+      w >>= 1;
+      wa -= 1;
+      if (group) {  // the run: j zero bits, then the newly significant coefficient's 1
+        int j = w ? ctz64(w) : 64;
+        if (j >= wa) {
+          w = rd.peek();
+          wa = 64;
+          j = w ? ctz64(w) : 64;
+        }
+        if (j >= 64 - n) return false;
+        rd.pos += j + 1;
+        if (j < 63) {
+          w >>= j + 1;
+          wa -= j + 1;
+        } else {
+          w = 0ull;
+          wa = 0;
+        }
+        m |= 1ull << (n + j);
+        n += j + 1;
+        continue;
+      }
+    }
+    sink(b, m);  // plane b is complete
+    if (--b < blast) break;
+    m = 0ull;
     if (n > 0) {  // the bits of the coefficients already significant, verbatim
-      if (rd.pos + n > rd.end) return false;
       if (wa < n) {
         w = rd.peek();
         wa = 64;
@@ -452,37 +432,6 @@ FZ_HD bool decode_planes_mem(R& rd, int minexp, K& sink, int& emax, int& planes)
         wa = 0;
       }
     }
-    while (n < 64) {
-      if (rd.pos + 1 > rd.end) return false;
-      if (wa < 1) {
-        w = rd.peek();
-        wa = 64;
-      }
-      const bool group = (w & 1ull) != 0ull;
-      rd.pos += 1;
-      w >>= 1;
-      wa -= 1;
-      if (!group) break;
-      // the run: j zero bits, then the newly significant coefficient's 1
-      int j = w ? ctz64(w) : 64;
-      if (j >= wa) {
-        w = rd.peek();
-        wa = 64;
-        j = w ? ctz64(w) : 64;
-      }
-      if (j >= 64 - n || rd.pos + j + 1 > rd.end) return false;
-      rd.pos += j + 1;
-      if (j < 63) {
-        w >>= j + 1;
-        wa -= j + 1;
-      } else {
-        w = 0ull;
-        wa = 0;
-      }
-      m |= 1ull << (n + j);
-      n += j + 1;
-    }
-    sink(b, m);
   }
   return true;
 }
