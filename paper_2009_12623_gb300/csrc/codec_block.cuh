@@ -57,6 +57,14 @@ FZ_HD float as_float(uint32_t u) {
   return f;
 #endif
 }
+// x rounded toward zero to an integer (|x| < 2^31)
+FZ_HD int trunc_to_int(float x) {
+#ifdef __CUDA_ARCH__
+  return __float2int_rz(x);
+#else
+  return (int)x;
+#endif
+}
 
 // ---- coefficient order (ascending total sequency, ties x-fastest) ----------
 struct PermTable {
@@ -230,16 +238,16 @@ FZ_HD bool quantise_coeffs(uint32_t* u, int minexp, int& emax, int& planes) {
     for (int i = 0; i < 64; ++i) u[i] = 0u;
     return finite;
   }
-  // q = trunc(x 2^(S - emax)) from the integer significand, exactly (in place)
+  // q = trunc(x 2^(S - emax)) (in place).  |x| < 2^emax, so |q| < 2^S.
+  // Scaling by a power of two is exact whenever the product is a normal
+  // number; a product that is not (subnormal or flushed to zero) is below 1
+  // in magnitude and truncates to 0 either way.  2^(S - emax) is applied as
+  // two normal factors because S - emax can exceed 127.
+  const int k = kS - emax;  // -103 .. 152
+  const int k1 = k < 127 ? k : 127;
+  const float s1 = as_float((uint32_t)(k1 + 127) << 23), s2 = as_float((uint32_t)(k - k1 + 127) << 23);
 #pragma unroll
-  for (int i = 0; i < 64; ++i) {
-    const uint32_t bits = u[i];
-    const int Eb = (int)((bits >> 23) & 0xffu);
-    const uint32_t M = Eb ? ((bits & 0x7fffffu) | 0x800000u) : (bits & 0x7fffffu);
-    const int sh = (Eb ? Eb : 1) - (150 - kS) - emax;
-    const uint32_t mag = sh >= 0 ? (M << sh) : (sh > -32 ? (M >> (-sh)) : 0u);
-    u[i] = (bits >> 31) ? (0u - mag) : mag;
-  }
+  for (int i = 0; i < 64; ++i) u[i] = (uint32_t)trunc_to_int((as_float(u[i]) * s1) * s2);
   xform_fwd(u);
   // sequency order and negabinary, through a register permutation
   uint32_t c[64];
