@@ -4,7 +4,9 @@
 // kernels use, and writes what it codes and decodes to stdout.
 //   stdin : int32 minexp, int32 n, then n blocks of 64 uint32 (FP32 bits, x fastest)
 //   stdout: per block int32 nbits, int32 nwords, nwords uint64, 64 uint32 decoded bits,
-//           int32 ok (decoder accepted the block and consumed exactly nbits)
+//           int32 ok (decoder accepted the block and consumed exactly nbits),
+//           int32 cut_ok, int32 long_ok (the same block declared one bit shorter or one bit
+//           longer than it is was accepted: both must be 0)
 #include <math.h>
 
 #include <cstdint>
@@ -98,6 +100,15 @@ int main() {
     int demax = 0, dplanes = 0;
     Sink sink{dlo, dhi};
     int32_t ok = decode_planes_mem(rd, minexp, sink, demax, dplanes) && rd.pos == nbits ? 1 : 0;
+    int32_t wrong_len_ok[2];
+    for (int w = 0; w < 2; ++w) {
+      const long end = w ? nbits + 1 : nbits - 1;
+      uint32_t xlo[32] = {0}, xhi[32] = {0};
+      Reader rx{wr.w.data(), 0, end, nwords};
+      Sink sx{xlo, xhi};
+      int xe = 0, xp = 0;
+      wrong_len_ok[w] = decode_planes_mem(rx, minexp, sx, xe, xp) && rx.pos == end ? 1 : 0;
+    }
     uint32_t q[64];
     for (int b = 0; b < 32; ++b) {
       const bool coded = b >= 32 - dplanes;
@@ -111,6 +122,7 @@ int main() {
     fwrite(wr.w.data(), 8, wr.w.size(), stdout);
     fwrite(v, 4, 64, stdout);
     fwrite(&ok, 4, 1, stdout);
+    fwrite(wrong_len_ok, 4, 2, stdout);
   }
   return 0;
 }

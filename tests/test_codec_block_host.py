@@ -64,9 +64,9 @@ def _harness(exe, minexp, blocks):
         off += 8 * nwords
         vals = np.frombuffer(raw, np.uint32, 64, off)
         off += 256
-        (ok,) = struct.unpack_from("<i", raw, off)
-        off += 4
-        res.append((nbits, words, vals, ok))
+        ok, cut_ok, long_ok = struct.unpack_from("<iii", raw, off)
+        off += 12
+        res.append((nbits, words, vals, (ok, cut_ok, long_ok)))
     assert off == len(raw)
     return res
 
@@ -96,7 +96,9 @@ def test_block_code_matches_oracle(oracle, harness, atol):
     assert all(r[0] == minexp for r in ref)
     got = _harness(harness, minexp, blocks)
     for (nbits, words, vals, ok), (_, o_nbits, o_words, o_dec), b in zip(got, ref, blocks):
-        assert ok == 1
+        # accepted at its coded length, rejected when declared one bit shorter or longer (the
+        # decoder checks the block's bounds once, against the bits it consumed)
+        assert ok == (1, 0, 0)
         assert nbits == o_nbits
         assert np.array_equal(words, o_words)
         assert np.array_equal(vals, o_dec.reshape(-1).view(np.uint32))
