@@ -213,12 +213,17 @@ def kernel_bytes(cells, enc_bytes_per_launch, live=1.0, image_in_decoder=False):
 
 
 def source_hash(kernel: str) -> str:
-    files = {"stencil_forward": "stencil.cu", "stencil_adjoint": "stencil.cu",
-             "zfp_encode": "codec.cu", "zfp_decode": "codec.cu"}
-    csrc = os.path.join(ROOT, "paper_2009_12623_gb300", "csrc")
+    """Hash of the sources the kernel's translation unit compiles: its .cu
+    file and the project headers it includes."""
+    csrc = os.path.join("paper_2009_12623_gb300", "csrc")
+    common = [os.path.join(csrc, "common.cuh"), os.path.join("include", "fwi.h")]
+    files = {"stencil_forward": [os.path.join(csrc, "stencil.cu")],
+             "stencil_adjoint": [os.path.join(csrc, "stencil.cu")],
+             "zfp_encode": [os.path.join(csrc, "codec.cu"), os.path.join(csrc, "codec_block.cuh")],
+             "zfp_decode": [os.path.join(csrc, "codec.cu"), os.path.join(csrc, "codec_block.cuh")]}
     h = hashlib.sha256()
-    for f in sorted({files[kernel], "codec_block.cuh", "common.cuh"}):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in files[kernel] + common:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
