@@ -367,8 +367,8 @@ FZ_HD void emit_mem(W& w, const P& pl, int emax, int planes) {
 // verbatim bits, so a lane's passes follow its own block's runs rather than
 // the warp's largest run count in every plane.  Whatever the bits, the loop
 // stops after at most 64 runs and one pass per plane; the bounds are checked
-// once, by the caller, which rejects the block unless exactly end - pos bits
-// were consumed.  Returns false on a malformed header or run.
+// once, by the caller, which rejects the block unless the reader stops
+// exactly at end.  Returns false on a malformed header or run.
 template <class R, class K>
 FZ_HD bool decode_planes_mem(R& rd, int minexp, K& sink, int& emax, int& planes) {
   emax = 0;
