@@ -60,18 +60,24 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Shared-memory bit writer (words assembled with atomicOr, so neighbouring
-// threads may share a boundary word).
+// Shared-memory bit writer over a zeroed buffer.  Neighbouring threads share
+// at most a boundary word: a thread's first word (which may hold the previous
+// thread's last bits) and its last, partial word are merged with atomicOr;
+// the words in between are the thread's alone and are stored.
 struct SWriter {
   unsigned long long* buf;
   unsigned long long acc;
   int fill;
   int word;
+  int first;  // the thread's first word
   __device__ __forceinline__ void put(unsigned long long v, int k) {  // 1 <= k <= 64
     acc |= v << fill;
     int nf = fill + k;
     if (nf >= 64) {
-      atomicOr(&buf[word], acc);
+      if (word == first)
+        atomicOr(&buf[word], acc);
+      else
+        buf[word] = acc;
       ++word;
       acc = fill ? (v >> (64 - fill)) : 0ull;
       nf -= 64;
@@ -223,7 +229,7 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, 4) k_encode_chained(EncArgs
   for (unsigned w = lane; w < W; w += 32) sbuf[w] = 0ull;
   __syncwarp();
   if (valid) {
-    SWriter wr{sbuf, 0ull, (int)(my_off & 63u), (int)(my_off >> 6)};
+    SWriter wr{sbuf, 0ull, (int)(my_off & 63u), (int)(my_off >> 6), (int)(my_off >> 6)};
     emit(wr, u, emax, planes);
     wr.flush();
   }
@@ -377,7 +383,7 @@ __global__ void __launch_bounds__(ZC_CHUNK * kWarps, FWI_ENC_MIN_CTAS) k_encode_
   for (unsigned w = lane; w < W; w += 32) buf[w] = 0ull;
   __syncwarp();
   if (valid) {
-    SWriter wr{buf, 0ull, (int)(my_off & 63u), (int)(my_off >> 6)};
+    SWriter wr{buf, 0ull, (int)(my_off & 63u), (int)(my_off >> 6), (int)(my_off >> 6)};
     emit_mem(wr, mine, emax, planes);
     wr.flush();
   }

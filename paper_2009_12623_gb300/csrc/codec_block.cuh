@@ -327,7 +327,14 @@ FZ_HD void emit(W& w, const uint32_t* u, int emax, int planes) {
   }
 }
 
-// emit with the plane masks in memory (P(b) returns plane b).
+// emit with the plane masks in memory (P(b) returns plane b).  A plane's
+// group-coded part is assembled in a 128-bit register pair (lo, hi) and
+// written with one or two puts: its first group bit 1, then the bits of
+// r = m >> n up to r's highest set bit, each set bit followed by a group bit
+// (1 while another set bit follows, else the final 0, which is left out when
+// the last set bit is coefficient 63).  A set bit of r at position p with i
+// set bits below it lands at s = 1 + p + i, its group bit at s + 1; at most
+// 128 bits (64 set bits from n = 0).
 template <class W, class P>
 FZ_HD void emit_mem(W& w, const P& pl, int emax, int planes) {
   if (planes == 0) {
@@ -339,22 +346,42 @@ FZ_HD void emit_mem(W& w, const P& pl, int emax, int planes) {
   for (int b = 31; b >= 32 - planes; --b) {
     const uint64_t m = pl(b);
     if (n > 0) w.put(n < 64 ? (m & ((1ull << n) - 1ull)) : m, n);
-    uint64_t r = n < 64 ? (m >> n) : 0ull;
-    while (n < 64) {
-      if (!r) {
-        w.put(0ull, 1);
-        break;
-      }
-      const int j = ctz64(r);
-      if (j < 63) {
-        w.put(1ull | (1ull << (j + 1)), j + 2);  // group bit, then the run up to the 1
-      } else {
-        w.put(1ull, 1);
-        w.put(1ull << j, j + 1);
-      }
-      n += j + 1;
-      r = (j + 1 < 64) ? (r >> (j + 1)) : 0ull;
+    if (n >= 64) continue;
+    uint64_t t = m >> n;
+    if (!t) {
+      w.put(0ull, 1);  // no newly significant coefficient
+      continue;
     }
+    uint64_t lo = 1ull, hi = 0ull;
+    int i = 0, s = 0;
+    do {
+      const int p = ctz64(t);
+      t &= t - 1ull;
+      s = 1 + p + i;
+      if (s < 63) {
+        lo |= 3ull << s;
+      } else if (s == 63) {
+        lo |= 1ull << 63;
+        hi |= 1ull;
+      } else {
+        hi |= 3ull << (s - 64);
+      }
+      ++i;
+    } while (t);
+    // the last set bit's group bit is the final 0 (or absent)
+    if (s + 1 < 64)
+      lo &= ~(1ull << (s + 1));
+    else if (s + 1 < 128)
+      hi &= ~(1ull << (s + 1 - 64));
+    const int nend = n + (s - i) + 1;  // coefficients significant after this plane
+    const int len = s + 1 + (nend < 64 ? 1 : 0);
+    if (len <= 64) {
+      w.put(lo, len);
+    } else {
+      w.put(lo, 64);
+      w.put(hi, len - 64);
+    }
+    n = nend;
   }
 }
 

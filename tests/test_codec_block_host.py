@@ -107,3 +107,18 @@ def test_block_code_matches_oracle(oracle, harness, atol):
         emax = np.frexp(np.float64(np.abs(b).max()))[1]
         bound = max(atol, 2.0 ** (emax - 24))
         assert np.all(np.abs(vals.view(np.float32).astype(np.float64) - b.reshape(-1)) <= bound)
+
+
+def test_embedded_coder_edges(tmp_path):
+    """The coder's group-coded assembly at its edges: all 64 coefficients
+    significant in the top plane (128 bits), coefficient 63 alone, runs that
+    end at 63, plus 2000 random plane sets -- bit for bit against a direct
+    restatement of the group coding, the exact bit count, and the decoder."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no C++ compiler")
+    exe = str(tmp_path / "emit_edge_check")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-x", "c++", os.path.join(HERE, "host", "emit_edge_check.cpp"),
+                    "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.startswith("ok "), out.stdout
